@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the ray-traced Gaussian rendering path (RaySplats, arXiv 2501.19196) on GB300.
+
+One step = one training pass of the whole path over one batch: LBVH rebuild + forward render
++ adjoint for every camera of the workload.  Default workload: 1,000,000 Gaussians (clustered
+scene with a background shell) seen by 16 ring cameras of mixed resolution
+(8 x 1280x832, 4 x 960x640, 4 x 640x416 = 12,042,240 rays); headline path: one persistent
+launch per pass, captured with the rebuild in a CUDA graph.
+
+Prints ONE JSON line (rank 0).  `value` is the device-timed fwd+bwd throughput (Mrays/s) of
+the batched path; the line also carries the plain (one launch per camera) numbers, fwd-only
+numbers, an end-to-end number through host buffers, the roofline of the dominant kernel, the
+SM clocks seen during the timed region and the oracle timed on the host cores.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s fwd and fwd+bwd at 1M Gaussians, batched vs plain, at oracle tolerance"
+L2_FLUSH_BYTES = 256 << 20
+
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, scaled to a
+# full launch (see profiles/); valid only while the kernel source hash matches.
+TRAFFIC = {"render.cu": None, "fwd_bytes": None, "bwd_bytes": None}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", type=int, default=4, help="1..4 (see workloads.scenes.workload)")
+    p.add_argument("--case", choices=["full", "small"], default="full",
+                   help="small: 1M Gaussians, two 640x416 cameras (for ncu captures)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--kbuf", type=int, default=None)
+    p.add_argument("--leaf", type=int, default=None)
+    p.add_argument("--tile-w", type=int, default=None)
+    return p.parse_args()
+
+
+def src_hash(name):
+    with open(os.path.join(ROOT, "paper_2501_19196_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * (max(smax) if smax else 1)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------
+def make_workload(args):
+    from workloads import scenes
+    wl = scenes.workload(args.workload)
+    if args.case == "small":
+        cams = scenes.concat_cameras([scenes.look_at_camera((12.0, 2.0, 0.0), (0, 0, 0), 640, 416, 60.0),
+                                      scenes.look_at_camera((0.0, 2.0, 12.0), (0, 0, 0), 640, 416, 60.0)])
+        wl = scenes.Workload(wl.name + "_small2cams", wl.scene, cams, wl.Q, wl.eps1, wl.k_max, wl.background, True)
+    return wl
+
+
+def oracle_sample_pixels(wl, n_rays, seed=5):
+    """Stratified pixel sample over all cameras (proportional to each camera's pixel count)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    npx = wl.cams.n_pixels()
+    cam = rng.choice(wl.cams.count, size=n_rays, p=npx / npx.sum()).astype(np.int32)
+    px = (rng.random(n_rays) * wl.cams.width[cam]).astype(np.int32)
+    py = (rng.random(n_rays) * wl.cams.height[cam]).astype(np.int32)
+    return cam, px, py
+
+
+def cpu_oracle_rate(wl, seconds, threads=None):
+    """Oracle (fwd + gradient) on a bounded ray sample of the workload: Mrays/s on the host."""
+    import numpy as np
+    import oracle
+    threads = threads or oracle.default_threads()
+    n = 64
+    while True:
+        cam, px, py = oracle_sample_pixels(wl, n)
+        rng = np.random.default_rng(1)
+        gc, ga = rng.standard_normal((n, 3)), rng.standard_normal(n)
+        t0 = time.perf_counter()
+        oracle.render(wl.scene, wl.cams, cam, px, py, wl.Q, wl.eps1, wl.k_max, wl.background, dl_rgb=gc,
+                      dl_alpha=ga, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * seconds or n >= 1 << 20:
+            return n / dt / 1e6, n, dt, threads
+        n = int(min(n * max(2.0, 0.8 * seconds / max(dt, 1e-3)), 1 << 20))
+
+
+# ------------------------------------------------------------------------------------------
+# reference arm: the oracle, as it stands, on the host cores
+# ------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = make_workload(args)
+    import oracle
+    threads = oracle.default_threads()
+    rate, n, dt, _ = cpu_oracle_rate(wl, seconds=min(args.cpu_seconds, 8.0), threads=threads)
+    import numpy as np
+    times = []
+    for s in range(args.warmup + args.steps):
+        cam, px, py = oracle_sample_pixels(wl, n, seed=100 + s)
+        rng = np.random.default_rng(s)
+        t0 = time.perf_counter()
+        oracle.render(wl.scene, wl.cams, cam, px, py, wl.Q, wl.eps1, wl.k_max, wl.background,
+                      dl_rgb=rng.standard_normal((n, 3)), dl_alpha=rng.standard_normal(n), threads=threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    mean = sum(times) / len(times)
+    value = n / mean / 1e6
+    sample = f"{n} rays per step, stratified over the {wl.cams.count} cameras, fwd + gradient, brute force"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "gaussians": wl.scene.n, "cameras": wl.cams.count,
+                   "rays_per_step": int(wl.cams.total_rays()), "path": "FP64 CPU oracle (brute force)"},
+        "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2501_19196_gb300 import Renderer, RenderParams, native
+    from workloads import scenes
+
+    native.load()
+    wl = make_workload(args)
+    dev = torch.device("cuda", local)
+    host = [np.ascontiguousarray(a, np.float32) for a in (wl.scene.means, wl.scene.quats, wl.scene.scales,
+                                                         wl.scene.opacities, wl.scene.rgb)]
+    params = [torch.from_numpy(a).to(dev) for a in host]
+    P = int(wl.cams.total_rays())
+    g_rgb_h, g_alpha_h = scenes.upstream_grad(P, seed=1)
+    d_rgb = torch.from_numpy(g_rgb_h).to(dev)
+    d_alpha = torch.from_numpy(g_alpha_h).to(dev)
+    prm = RenderParams(Q=wl.Q, eps1=wl.eps1, background=wl.background, k_max=wl.k_max)
+    overrides = {}
+    if args.kbuf:
+        overrides["kbuf"] = args.kbuf
+    if args.leaf:
+        overrides["leaf_size"] = args.leaf
+    if args.tile_w:
+        overrides["tile_w"] = args.tile_w
+    tune_b = native.default_tune(persistent=1, **overrides)
+    tune_p = native.default_tune(persistent=0, **overrides)
+    n = wl.scene.n
+    outs = (torch.empty((P, 3), device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
+    grads = {"means": torch.zeros((n, 3), device=dev), "quats": torch.zeros((n, 4), device=dev),
+             "scales": torch.zeros((n, 3), device=dev), "opacities": torch.zeros(n, device=dev),
+             "rgb": torch.zeros((n, 3), device=dev)}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    rb = Renderer(tune=tune_b, Q_box=wl.Q)
+    rp = Renderer(tune=tune_p, Q_box=wl.Q)
+    rb.set_cameras(wl.cams)
+    rp.set_cameras(wl.cams)
+
+    def step(r, backward=True):
+        r.build(*params)
+        r.render(None, prm, out=outs)
+        if backward:
+            for t in grads.values():
+                t.zero_()
+            r.backward(d_rgb, d_alpha, grads=grads)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        if sampler:
+            sampler.start()
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # L2 flush (untimed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clocks
+
+    # --- warm up both renderers eagerly (allocations happen here) ---
+    step(rb)
+    step(rp)
+    rb.check_device()
+    rp.check_device()
+
+    # --- CUDA graphs: rebuild + fwd + bwd, and rebuild + fwd ---
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            fn()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            fn()
+        torch.cuda.synchronize()
+        return g
+
+    g_fb = capture(lambda: step(rb, True))
+    g_f = capture(lambda: step(rb, False))
+
+    sampler = ClockSampler(local)
+    ms_fb, clocks = timed(g_fb.replay, args.steps, args.warmup, sampler)
+    ms_f, _ = timed(g_f.replay, args.steps, args.warmup)
+    rb.check_device()
+    ms_fb_nograph, _ = timed(lambda: step(rb, True), max(3, args.steps // 2), 1)
+    plain = {}
+    if not args.no_plain:
+        ms_p_fb, _ = timed(lambda: step(rp, True), max(3, args.steps // 2), 1)
+        ms_p_f, _ = timed(lambda: step(rp, False), max(3, args.steps // 2), 1)
+        rp.check_device()
+        plain = {"fwd_bwd_mrays_s": P / ms_p_fb / 1e3 * world, "fwd_mrays_s": P / ms_p_f / 1e3 * world,
+                 "ms_per_step_fwd_bwd": ms_p_fb, "ms_per_step_fwd": ms_p_f,
+                 "launches_per_step": "one forward and one backward launch per camera"}
+
+    # --- per-kernel durations (events on the launching stream), batched path ---
+    kt = {"build": [], "fwd": [], "bwd": []}
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        rb.build(*params)
+        ev[1].record(stream)
+        rb.render(None, prm, out=outs)
+        ev[2].record(stream)
+        for t in grads.values():
+            t.zero_()
+        rb.backward(d_rgb, d_alpha, grads=grads)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        kt["build"].append(ev[0].elapsed_time(ev[1]))
+        kt["fwd"].append(ev[1].elapsed_time(ev[2]))
+        kt["bwd"].append(ev[2].elapsed_time(ev[3]))
+    kms = {k: sum(v) / len(v) for k, v in kt.items()}
+
+    # --- traversal counters (instrumented kernels, same inputs) ---
+    stats_f = torch.zeros(8, dtype=torch.int64, device=dev)
+    stats_b = torch.zeros(8, dtype=torch.int64, device=dev)
+    rb.build(*params)
+    rb.render(None, prm, out=outs, stats=stats_f)
+    for t in grads.values():
+        t.zero_()
+    rb.backward(d_rgb, d_alpha, grads=grads, stats=stats_b)
+    torch.cuda.synchronize()
+    rb.check_device()
+    sf = dict(zip(native.STATS_FIELDS, stats_f.cpu().tolist()))
+    sb = dict(zip(native.STATS_FIELDS, stats_b.cpu().tolist()))
+    # algorithmic bytes per launch: node 64 B, test record 48 B, shade 16 B,
+    # outputs + state 36 B per ray; backward: replayed hit 64 B record + 64 B atomics, 32 B per ray
+    fwd_bytes = 64 * sf["nodes_visited"] + 48 * sf["gaussians_tested"] + 16 * sf["hits_composited"] + 36 * sf["rays"]
+    bwd_bytes = 64 * sb["nodes_visited"] + 48 * sb["gaussians_tested"] + 128 * sb["hits_composited"] + 32 * sb["rays"]
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    dom = "bwd" if kms["bwd"] >= kms["fwd"] else "fwd"
+    dom_bytes = bwd_bytes if dom == "bwd" else fwd_bytes
+    achieved = dom_bytes / (kms[dom] * 1e-3) / 1e9
+    traffic = None
+    if TRAFFIC.get("render.cu") == src_hash("render.cu"):
+        traffic = TRAFFIC["bwd_bytes" if dom == "bwd" else "fwd_bytes"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": traffic, "kernel": "k_render_bwd (persistent)" if dom == "bwd" else
+                "k_render_fwd (persistent)", "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": dom_bytes, "kernel_ms": kms[dom],
+                "counts_fwd": sf, "counts_bwd": sb,
+                "min_bytes_fraction": (64 * sf["hits_composited"] + 36 * sf["rays"]) / (kms["fwd"] * 1e-3) / 1e9 / hbm}
+
+    # --- end to end through host buffers (pinned) ---
+    e2e = None
+    if not args.no_e2e:
+        pinned_in = [torch.from_numpy(a).pin_memory() for a in host] + \
+                    [torch.from_numpy(g_rgb_h).pin_memory(), torch.from_numpy(g_alpha_h).pin_memory()]
+        dev_in = params + [d_rgb, d_alpha]
+        pinned_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
+        h2d = sum(t.numel() * t.element_size() for t in pinned_in)
+        d2h = sum(t.numel() * t.element_size() for t in pinned_out.values())
+
+        def e2e_step():
+            for h, d in zip(pinned_in, dev_in):
+                d.copy_(h, non_blocking=True)
+            g_fb.replay()
+            for k, v in grads.items():
+                pinned_out[k].copy_(v, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        barrier()
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+        e2e = {"value": P / ms_e2e / 1e3 * world, "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+               "path": "pinned host params + dL -> device, graph replay, gradients -> pinned host"}
+
+    # --- CPU oracle baseline (rank 0) ---
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, nr, dt, thr = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
+               "sample": f"{nr} stratified rays of the same workload, fwd + gradient, FP64 brute force, {dt:.1f} s"}
+
+    launches_build = 3 + 3 * (8 if tune_b.morton_bits == 21 else 4) + 3
+    gpu_launches = args.steps * (launches_build + 1 + 2)
+    value = P / ms_fb / 1e3 * world
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "gaussians": n, "cameras": wl.cams.count, "rays_per_step": P,
+                   "step": "LBVH rebuild + forward render + adjoint, all cameras",
+                   "path": "batched: one persistent forward and one persistent backward launch, CUDA graph",
+                   "tune": tune_b.as_dict(), "l2": "flushed between timed steps (256 MiB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "fwd_mrays_s": P / ms_f / 1e3 * world, "ms_per_step_fwd": ms_f,
+        "fwd_bwd_mrays_s_no_graph": P / ms_fb_nograph / 1e3 * world,
+        "plain": plain,
+        "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
+        "kernel_ms": kms,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    rb.close()
+    rp.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * raysplats.h -- C ABI of the GB300 (sm_103a) RaySplats rendering path.
+ *
+ * The library renders images by tracing camera rays through a scene of 3D Gaussians held as
+ * confidence ellipsoids with an opacity and an RGB colour, and computes the adjoint of that
+ * render.  Paper: RaySplats (arXiv 2501.19196).  What each call computes:
+ *   - the scene: G = {(N(m_i, Sigma_i), opacity_i, c_i)}, Sigma = R S S^T R^T    (Eq. 1, Eq. 2)
+ *   - a ray hits Gaussian i when it meets the confidence ellipsoid
+ *     (x - m)^T Sigma^-1 (x - m) = Q at an entry parameter t1 >= t_near          (Sec. 3, Prop. 1)
+ *   - each hit contributes alpha_i = opacity_i * exp(-D_i^2 / 2), D_i^2 the squared
+ *     Mahalanobis distance of the ray from m_i (the maximum response)           (Eq. 8, Prop. 2)
+ *   - hits are composited front to back in (t1, id) order, C = sum c_i alpha_i T_i, T_i =
+ *     prod_{j<i}(1 - alpha_j); the hit that brings T below eps1 is the last, and at most
+ *     k_max hits are composited                                                 (Eq. 3, Sec. 3)
+ *   - the backward pass is the exact derivative of that render                  (App. A.3-A.6)
+ *
+ * Conventions for every call:
+ *   - All pointers marked "device" are CUDA device pointers on the current device; all sizes
+ *     are element counts.  The caller owns every parameter, output and gradient buffer.
+ *   - The library owns rs_accel and rs_fwd_state (opaque handles).  Passing a pointer to a
+ *     NULL handle creates one; passing an existing handle reuses (and if needed grows) its
+ *     device memory, so repeated calls with the same sizes allocate nothing (required for
+ *     CUDA-graph capture).
+ *   - Every call is stream ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and asynchronous; nothing is synchronised except where stated.  Nothing throws
+ *     across the ABI: each call returns an rs_status and records a message for
+ *     rs_last_error() (per host thread).
+ *   - Arguments are validated on the host before any launch (RS_ERR_INVALID_ARG).  Device-side
+ *     consistency checks set an error word that rs_check_device() reports.
+ */
+#ifndef RAYSPLATS_H
+#define RAYSPLATS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RS_ABI_VERSION 1
+
+typedef int32_t rs_status;
+enum {
+    RS_OK = 0,
+    RS_ERR_INVALID_ARG = -1, /* a NULL pointer, a bad size or an out-of-range parameter */
+    RS_ERR_OOM = -2,         /* device or pinned-host allocation failed */
+    RS_ERR_CUDA = -3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    RS_ERR_UNSUPPORTED = -4, /* valid request this build does not implement */
+    RS_ERR_INTERNAL = -5,    /* a device-side consistency check failed */
+    RS_ERR_TIMEOUT = -6      /* reserved: a bounded device wait gave up (no kernel waits today) */
+};
+
+/* Scene (Eq. 1, Eq. 2).  Structure of arrays, FP32, all device pointers, n >= 1:
+ *   means[3n]      m_i
+ *   quats[4n]      (w, x, y, z) rotation quaternion, need not be normalised (R uses
+ *                  s = 2/|q|^2, App. A.6); must be non-zero
+ *   scales[3n]     physical scales s_i > 0 (S = diag(s)); activations such as exp/sigmoid are
+ *                  the caller's
+ *   opacities[n]   physical opacity in [0, 1); the backward pass needs 1 - alpha > 0
+ *   rgb[3n]        colour c_i */
+typedef struct {
+    int64_t n;
+    const float* means;
+    const float* quats;
+    const float* scales;
+    const float* opacities;
+    const float* rgb;
+} rs_gaussians;
+
+/* Pinhole camera (host struct).  world = R_wc * cam + pos; camera axes x right, y down,
+ * z forward.  Ray of pixel (u, v): direction normalise(R_wc * ((u + 0.5 - cx) / fx,
+ * (v + 0.5 - cy) / fy, 1)) evaluated as a fixed FP32 operation sequence (no fused
+ * multiply-add), origin pos.  width, height >= 1 and width * height < 2^31. */
+typedef struct {
+    float R_wc[9]; /* row major */
+    float pos[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} rs_camera;
+
+/* Render parameters (Sec. 3).
+ *   Q           squared Mahalanobis radius of the confidence ellipsoid, 0 < Q <= the accel's
+ *               Q_box (Q = F^-1_chi2(3)(confidence); 11.3449 for 0.99)
+ *   eps1        transmittance cut, >= 0
+ *   t_near      smallest accepted entry parameter t1, >= 0 (units of the unit-length ray)
+ *   background  added as T_final * background
+ *   k_max       at most k_max composited hits per ray, >= 1 (INT32_MAX = unbounded)
+ *   depth_mode  0: depth = sum_i w_i t1_i (unnormalised); other values unsupported
+ *   sort_key    0: order hits by (t1, id); other values unsupported */
+typedef struct {
+    float Q;
+    float eps1;
+    float t_near;
+    float background[3];
+    int32_t k_max;
+    int32_t depth_mode;
+    int32_t sort_key;
+} rs_render_params;
+
+/* Frame outputs, device, cameras concatenated in order, each camera row major (y, x):
+ *   rgb[3 * sum W*H], alpha[sum W*H], depth[sum W*H] (depth may be NULL). */
+typedef struct {
+    float* rgb;
+    float* alpha;
+    float* depth;
+} rs_frame;
+
+/* Upstream gradient (device, same layout as rs_frame): d_rgb required, d_alpha may be NULL. */
+typedef struct {
+    const float* d_rgb;
+    const float* d_alpha;
+} rs_frame_grad;
+
+/* Parameter gradients (device, same layout as rs_gaussians).  ACCUMULATED into (+=); the
+ * caller zeroes them.  Any pointer may be NULL to skip that gradient. */
+typedef struct {
+    float* d_means;
+    float* d_quats;
+    float* d_scales;
+    float* d_opacities;
+    float* d_rgb;
+} rs_gaussian_grads;
+
+/* Tunables.  None changes a result (tests check this), only speed.
+ *   tile_w, tile_h  ray tile handled by one warp; tile_w * tile_h == 32
+ *   kbuf            per-ray k-buffer depth: 8, 16 or 32
+ *   leaf_size       BVH leaf size 1..16 (used by rs_build_accel)
+ *   morton_bits     10 (30-bit codes) or 21 (63-bit codes) bits per axis
+ *   persistent      0: one launch per camera; 1: one persistent launch over all cameras'
+ *                   ray tiles through a device work queue
+ *   block_warps     warps per CTA: 1..16 */
+typedef struct {
+    int32_t tile_w, tile_h;
+    int32_t kbuf;
+    int32_t leaf_size;
+    int32_t morton_bits;
+    int32_t persistent;
+    int32_t block_warps;
+} rs_tune_params;
+
+typedef struct rs_accel rs_accel;
+typedef struct rs_fwd_state rs_fwd_state;
+
+/* Counters of the instrumented render (rs_render_counted): per-call sums over all rays. */
+typedef struct {
+    uint64_t rays;             /* rays traced */
+    uint64_t nodes_visited;    /* BVH nodes fetched (64 B each) */
+    uint64_t gaussians_tested; /* ray / ellipsoid tests (48 B record each) */
+    uint64_t hits_composited;  /* composited hits (16 B shade record each) */
+    uint64_t rounds;           /* k-buffer traversal rounds */
+    uint64_t hits_inserted;    /* candidates inserted into a k-buffer */
+    uint64_t reserved[2];
+} rs_render_stats;
+
+/* ABI version (RS_ABI_VERSION of the build). */
+int32_t rs_abi_version(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* rs_last_error(void);
+
+/* Fill *out with the default tunables (8x4 tiles, kbuf 16, leaf 4, 63-bit codes,
+ * persistent launch, 4 warps per CTA). */
+rs_status rs_default_tune(rs_tune_params* out);
+
+/* Build the acceleration structure of a scene (LBVH): per-Gaussian render records
+ * (M = S^-1 R^T and the mean, opacity and colour) and conservative boxes of the confidence
+ * ellipsoids |M (x - m)|^2 <= Q_box in Morton order, a 63- or 30-bit Morton sort, a Karras
+ * binary radix tree with leaves of at most leaf_size Gaussians, and a bottom-up box refit.
+ * Q_box > 0 bounds the Q of every rs_render that uses this accel.  *inout: NULL to create,
+ * else reused.  The accel reads the scene at build time only; rebuild after the parameters
+ * change. */
+rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_params* tune,
+                         rs_accel** inout, void* cuda_stream);
+
+/* Render n_cams cameras (host array) of the scene `g` through `accel` (built from the same
+ * scene).  Writes out->rgb / alpha / depth and, in *inout_state (NULL to create, else reused),
+ * what the backward pass needs: per ray the final transmittance, the (t1, id) key of the
+ * last composited hit and the hit count (16 B per ray), plus the cameras and parameters. */
+rs_status rs_render(const rs_gaussians* g, const rs_accel* accel, const rs_camera* cams,
+                    int32_t n_cams, const rs_render_params* params, const rs_tune_params* tune,
+                    rs_frame* out, rs_fwd_state** inout_state, void* cuda_stream);
+
+/* rs_render plus per-call counters: *stats_device (device memory, 8 uint64, zeroed by the
+ * caller) is incremented with the rs_render_stats fields.  Slower; for measurement only. */
+rs_status rs_render_counted(const rs_gaussians* g, const rs_accel* accel, const rs_camera* cams,
+                            int32_t n_cams, const rs_render_params* params,
+                            const rs_tune_params* tune, rs_frame* out,
+                            rs_fwd_state** inout_state, uint64_t* stats_device,
+                            void* cuda_stream);
+
+/* Adjoint of the last rs_render recorded in `state` (App. A.3-A.6): replays every ray back
+ * to front (re-traversing `accel`), recovers the transmittance from the stored final value,
+ * and ACCUMULATES dL/d(means, quats, scales, opacities, rgb) into `out`.  `g` and `accel`
+ * must be the ones the forward pass used. */
+rs_status rs_render_backward(const rs_gaussians* g, const rs_accel* accel,
+                             const rs_fwd_state* state, const rs_frame_grad* dl,
+                             const rs_tune_params* tune, rs_gaussian_grads* out,
+                             void* cuda_stream);
+
+/* rs_render_backward plus per-call counters of the replay traversal (same layout as
+ * rs_render_counted: rays, nodes visited, tests, replayed hits, rounds, inserted). */
+rs_status rs_render_backward_counted(const rs_gaussians* g, const rs_accel* accel,
+                                     const rs_fwd_state* state, const rs_frame_grad* dl,
+                                     const rs_tune_params* tune, rs_gaussian_grads* out,
+                                     uint64_t* stats_device, void* cuda_stream);
+
+/* Free a handle (NULL is accepted).  Synchronises the device before freeing. */
+rs_status rs_accel_destroy(rs_accel* accel);
+rs_status rs_state_destroy(rs_fwd_state* state);
+
+/* Synchronise `cuda_stream` and report the device error words of accel/state (either may be
+ * NULL): RS_ERR_INTERNAL with a message if a device consistency check failed, else RS_OK.
+ * Clears the words. */
+rs_status rs_check_device(const rs_accel* accel, const rs_fwd_state* state, void* cuda_stream);
+
+/* ---- Introspection (tests and tooling) -------------------------------------------------- */
+
+/* Copy the LBVH of `accel` to host arrays (synchronises).  Each pointer may be NULL.
+ *   codes[n]   sorted Morton codes          perm[n]   sorted position -> Gaussian id
+ *   first[n-1], last[n-1], split[n-1]   Karras internal node ranges and split positions
+ *   boxes[6 * (n-1)]  internal node boxes (lo xyz, hi xyz)   prim_boxes[6n] per sorted
+ *   Gaussian, lo_hi[6] scene bounds of the means.  *n_out receives n. */
+rs_status rs_accel_export(const rs_accel* accel, int64_t* n_out, uint64_t* codes, uint32_t* perm,
+                          int32_t* first, int32_t* last, int32_t* split, float* boxes,
+                          float* prim_boxes, float* lo_hi);
+
+/* Generate the camera rays of n_rays listed pixels on the device (the exact FP32 operation
+ * sequence the renderer uses).  cam_idx/px/py: device int32[n_rays]; o, d: device float[3 n]. */
+rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays,
+                        const int32_t* cam_idx, const int32_t* px, const int32_t* py, float* o,
+                        float* d, void* cuda_stream);
+
+/* The renderer's ray/Gaussian test for n_pairs (ray r, sorted Gaussian j) pairs of `accel`:
+ * out[4 * k] = D^2, t1, hit (1/0), alpha (device floats). ray_o/ray_d device float[3 n_pairs],
+ * sorted_j device int32[n_pairs]. */
+rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o,
+                        const float* ray_d, const int32_t* sorted_j, float Q, float t_near,
+                        float* out, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAYSPLATS_H */

@@ -1,0 +1,644 @@
+// render.cu -- per-ray traversal, compositing and the adjoint (RaySplats, arXiv 2501.19196).
+//
+// Forward (a7-a9): each lane traces one camera ray.  A round traverses the LBVH with a
+// register k-buffer of the K nearest hits whose (t1, id) key lies beyond the last composited
+// key (nodes whose box entry lies past the K-th key are pruned), then composites those hits
+// front to back (Eq. 3) with alpha = opacity * exp(-D2/2) (Prop. 2), stopping after the hit
+// that brings T below eps1 or at k_max hits (Sec. 3).  A full buffer starts the next round.
+// Per ray it stores T_final, the last composited key and the hit count (16 B).
+//
+// Adjoint (a10): the same traversal with a descending k-buffer of the K farthest hits below
+// an upper key replays the composited hits back to front.  The transmittance before each hit
+// is recovered as T_i = T_{i+1} / (1 - alpha_i) from the stored T_final (the forward's
+// (1 - alpha_i) is recomputed bit for bit, so the rounding cancels), and the colour behind a
+// hit follows U_{i-1} = alpha_i c_i + (1 - alpha_i) U_i, giving dC/dalpha_i = T_i (c_i - U_i)
+// without the division of App. A.4/A.5.  The chain through D2 (App. A.6) uses the envelope
+// form dD2/dM = 2 p v^T, dD2/dm = -2 M^T p; per-hit contributions go to a 16-float-per-
+// Gaussian accumulator with float4 atomics, and a finalize kernel maps dL/dM to the
+// quaternion and scales through M = S^-1 R(q)^T.
+//
+// Launch modes: plain (one launch per camera, one warp per 32-ray tile) and persistent (one
+// launch over every camera's tiles, warps pull tiles from a device counter).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rs_internal.cuh"
+#include "rs_render.h"
+
+namespace rs {
+
+__device__ __forceinline__ float safe_rcp(float x) {
+    const float ax = fabsf(x);
+    return __frcp_rn(ax > 1e-30f ? x : copysignf(1e-30f, x));
+}
+
+// Both children's boxes against [tlo, thi]; the computed entry/exit are widened by 1e-6
+// relative so that rounding can never prune a box that holds a hit inside [tlo, thi].
+__device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const float4 n2, const float3 o,
+                                      const float3 inv, float tlo, float thi, bool& h0, bool& h1,
+                                      float& e0, float& e1) {
+    {
+        const float a0 = (n0.x - o.x) * inv.x, b0 = (n0.y - o.x) * inv.x;
+        const float a1 = (n0.z - o.y) * inv.y, b1 = (n0.w - o.y) * inv.y;
+        const float a2 = (n2.x - o.z) * inv.z, b2 = (n2.y - o.z) * inv.z;
+        float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
+        float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
+        en = fmaf(-1e-6f, fabsf(en), en);
+        ex = fmaf(1e-6f, fabsf(ex), ex);
+        e0 = fmaxf(en, tlo);
+        h0 = e0 <= fminf(ex, thi);
+    }
+    {
+        const float a0 = (n1.x - o.x) * inv.x, b0 = (n1.y - o.x) * inv.x;
+        const float a1 = (n1.z - o.y) * inv.y, b1 = (n1.w - o.y) * inv.y;
+        const float a2 = (n2.z - o.z) * inv.z, b2 = (n2.w - o.z) * inv.z;
+        float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
+        float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
+        en = fmaf(-1e-6f, fabsf(en), en);
+        ex = fmaf(1e-6f, fabsf(ex), ex);
+        e1 = fmaxf(en, tlo);
+        h1 = e1 <= fminf(ex, thi);
+    }
+}
+
+// ascending k-buffer: keys[0] nearest; insert `key` (< keys[K-1]) by one bubble pass
+template <int K>
+__device__ __forceinline__ void kbuf_insert_asc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
+    keys[K - 1] = key;
+    d2[K - 1] = D2;
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) {
+        const bool sw = keys[s] < keys[s - 1];
+        const int64_t ka = keys[s - 1], kb = keys[s];
+        const float da = d2[s - 1], db = d2[s];
+        keys[s - 1] = sw ? kb : ka;
+        keys[s] = sw ? ka : kb;
+        d2[s - 1] = sw ? db : da;
+        d2[s] = sw ? da : db;
+    }
+}
+
+// descending k-buffer: keys[0] farthest; insert `key` (> keys[K-1])
+template <int K>
+__device__ __forceinline__ void kbuf_insert_desc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
+    keys[K - 1] = key;
+    d2[K - 1] = D2;
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) {
+        const bool sw = keys[s] > keys[s - 1];
+        const int64_t ka = keys[s - 1], kb = keys[s];
+        const float da = d2[s - 1], db = d2[s];
+        keys[s - 1] = sw ? kb : ka;
+        keys[s] = sw ? ka : kb;
+        d2[s - 1] = sw ? db : da;
+        d2[s] = sw ? da : db;
+    }
+}
+
+struct Counters {
+    uint32_t nodes = 0, tests = 0, hits = 0, rounds = 0, inserted = 0;
+};
+
+// One traversal round.  DESC = false: collect the K smallest keys > lo_key.  DESC = true:
+// collect the K largest keys < hi_key.  Pruning: box entry <= the t of the K-th kept key (or
+// of hi_key), box exit >= the t of lo_key (or of the K-th kept key).
+template <int K, bool DESC, bool COUNT>
+__device__ __forceinline__ void traverse_round(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                               const TraceParams& P, const float3 o, const float3 d,
+                                               const float3 inv, int64_t bound_key, int64_t (&keys)[K],
+                                               float (&d2)[K], Counters& cnt, int* err) {
+    int stack[kStackSize];
+    float stack_t[kStackSize];
+    int sp = 0;
+    int node = 0;
+    const float t_bound = DESC ? key_t(bound_key) : (bound_key < 0 ? P.t_near : key_t(bound_key));
+    int visits = 0;
+    while (true) {
+        if (++visits > P.max_visits) {
+            atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        const float4 n0 = __ldg(nodes + 4 * node + 0);
+        const float4 n1 = __ldg(nodes + 4 * node + 1);
+        const float4 n2 = __ldg(nodes + 4 * node + 2);
+        const float4 n3 = __ldg(nodes + 4 * node + 3);
+        if (COUNT) cnt.nodes++;
+        float tlo, thi;
+        if (!DESC) {
+            tlo = t_bound;
+            thi = keys[K - 1] == kEmptyKey ? __int_as_float(0x7f800000) : key_t(keys[K - 1]);
+        } else {
+            tlo = keys[K - 1] == kEmptyKeyDesc ? P.t_near : key_t(keys[K - 1]);
+            thi = t_bound;
+        }
+        bool h0, h1;
+        float e0, e1;
+        slab2(n0, n1, n2, o, inv, tlo, thi, h0, h1, e0, e1);
+        const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+        const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const bool hs = side ? h1 : h0;
+            const int rs_ = side ? r1 : r0;
+            if (hs && rs_ < 0) {
+                const int start = ~rs_, count = side ? c1 : c0;
+                for (int q = start; q < start + count; ++q) {
+                    const float4 g0 = __ldg(rec + 4 * q + 0);
+                    const float4 g1 = __ldg(rec + 4 * q + 1);
+                    const float4 g2 = __ldg(rec + 4 * q + 2);
+                    Hit h;
+                    ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                    if (COUNT) cnt.tests++;
+                    if (h.hit) {
+                        const int64_t key = pack_key(h.t1, q);
+                        if (!DESC) {
+                            if (key > bound_key && key < keys[K - 1]) {
+                                kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                if (COUNT) cnt.inserted++;
+                            }
+                        } else {
+                            if (key < bound_key && key > keys[K - 1]) {
+                                kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                if (COUNT) cnt.inserted++;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        const bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+        // current pruning bounds after the leaves of this node
+        float cur_lo, cur_hi;
+        if (!DESC) {
+            cur_lo = tlo;
+            cur_hi = keys[K - 1] == kEmptyKey ? __int_as_float(0x7f800000) : key_t(keys[K - 1]);
+        } else {
+            cur_lo = keys[K - 1] == kEmptyKeyDesc ? P.t_near : key_t(keys[K - 1]);
+            cur_hi = thi;
+        }
+        (void)cur_lo;
+        if (i0 && i1) {
+            // near child first (ascending) / far child first (descending)
+            const bool first0 = DESC ? (e0 >= e1) : (e0 <= e1);
+            const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
+            const float ts = first0 ? e1 : e0;
+            if (sp < kStackSize) {
+                stack[sp] = ns;
+                stack_t[sp] = ts;
+                ++sp;
+            } else {
+                atomicOr(err, kErrStack);
+            }
+            node = nf;
+        } else if (i0) {
+            node = r0;
+        } else if (i1) {
+            node = r1;
+        } else {
+            // pop, skipping boxes whose entry now lies past the ascending bound
+            bool found = false;
+            while (sp > 0) {
+                --sp;
+                if (DESC || stack_t[sp] <= cur_hi) {
+                    node = stack[sp];
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) break;
+        }
+    }
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                              const TraceParams& P, const float3 o, const float3 d, float& C0,
+                                              float& C1, float& C2, float& T, float& depth,
+                                              int64_t& last_key, int& count, Counters& cnt, int* err) {
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float eps = fmaxf(P.eps1, 1e-30f);
+    T = 1.f;
+    C0 = C1 = C2 = 0.f;
+    depth = 0.f;
+    count = 0;
+    last_key = -1;
+    int64_t lo_key = -1;
+    bool done = false;
+    int rounds = 0;
+    while (!done) {
+        if (++rounds > P.max_rounds) {
+            atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKey;
+            d2[s] = 0.f;
+        }
+        if (COUNT) cnt.rounds++;
+        traverse_round<K, false, COUNT>(rec, nodes, P, o, d, inv, lo_key, keys, d2, cnt, err);
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (!done) {
+                const int64_t key = keys[s];
+                if (key == kEmptyKey) {
+                    done = true;
+                } else {
+                    const int j = key_j(key);
+                    const float4 sh = __ldg(rec + 4 * j + 3);
+                    const float a = response_alpha(sh.x, d2[s]);
+                    const float w = __fmul_rn(T, a);
+                    C0 = fmaf(w, sh.y, C0);
+                    C1 = fmaf(w, sh.z, C1);
+                    C2 = fmaf(w, sh.w, C2);
+                    depth = fmaf(w, key_t(key), depth);
+                    T = __fmul_rn(T, __fsub_rn(1.f, a));
+                    ++count;
+                    last_key = key;
+                    if (COUNT) cnt.hits++;
+                    if (T < eps || count >= P.k_max) done = true;
+                }
+            }
+        }
+        if (!done) lo_key = keys[K - 1];
+    }
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                               const TraceParams& P, const float3 o, const float3 d, float T_final,
+                                               int64_t last_key, int n_hits, const float gC[3], float gA,
+                                               float4* __restrict__ gtmp, Counters& cnt, int* err) {
+    if (n_hits <= 0) return;
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    int64_t hi_key = last_key + 1;
+    float Tn = T_final;
+    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    int remaining = n_hits;
+    int rounds = 0;
+    while (remaining > 0) {
+        if (++rounds > P.max_rounds) {
+            atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        if (COUNT) cnt.rounds++;
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKeyDesc;
+            d2[s] = 0.f;
+        }
+        traverse_round<K, true, COUNT>(rec, nodes, P, o, d, inv, hi_key, keys, d2, cnt, err);
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            const int64_t key = keys[s];
+            if (remaining > 0 && key != kEmptyKeyDesc) {
+                const int j = key_j(key);
+                const float4 g0 = __ldg(rec + 4 * j + 0);
+                const float4 g1 = __ldg(rec + 4 * j + 1);
+                const float4 g2 = __ldg(rec + 4 * j + 2);
+                const float4 sh = __ldg(rec + 4 * j + 3);
+                Hit h;
+                ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                const float e = expf(__fmul_rn(-0.5f, h.D2));
+                const float a = __fmul_rn(sh.x, e);
+                const float om = __fsub_rn(1.f, a);
+                const float Ti = __fdiv_rn(Tn, om);
+                const float w = Ti * a;
+                // dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A))
+                const float dLda = Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) +
+                                         gA * (1.f - UA));
+                U0 = fmaf(a, sh.y, om * U0);
+                U1 = fmaf(a, sh.z, om * U1);
+                U2 = fmaf(a, sh.w, om * U2);
+                UA = fmaf(om, UA, a);
+                Tn = Ti;
+                const float gD2 = -0.5f * a * dLda;
+                const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+                // dL/dm = -M^T (2 gD2 p)
+                const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
+                const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+                const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+                float4* gp = gtmp + 4 * j;
+                atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
+                atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
+                atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
+                atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+                --remaining;
+                hi_key = key;
+                if (COUNT) cnt.hits++;
+            }
+        }
+        if (remaining > 0 && keys[K - 1] == kEmptyKeyDesc) {
+            atomicOr(err, kErrReplayMismatch);
+            break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int lane, DevCam& cam, int& px, int& py,
+                                           int64_t& pix) {
+    int c = A.cam_single;
+    int64_t local = tile;
+    if (A.cam_single < 0) {
+        c = 0;
+        while (c + 1 < A.n_cams && A.cams[c + 1].tile_base <= tile) ++c;
+        local = tile - A.cams[c].tile_base;
+    }
+    cam = A.cams[c];
+    const int tx = (int)(local % cam.tiles_x), ty = (int)(local / cam.tiles_x);
+    px = tx * A.tile_w + (lane % A.tile_w);
+    py = ty * (32 / A.tile_w) + (lane / A.tile_w);
+    pix = cam.pix_base + (int64_t)py * cam.W + px;
+    return px < cam.W && py < cam.H && ty < cam.tiles_y;
+}
+
+template <int K, bool PERSIST, bool COUNT>
+__global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
+    const int lane = threadIdx.x & 31;
+    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Counters cnt;
+    uint32_t rays = 0;
+    while (true) {
+        if (PERSIST) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(A.queue, 1ull);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (tile >= A.total_tiles) break;
+        DevCam cam;
+        int px, py;
+        int64_t pix;
+        if (tile_pixel(A, tile, lane, cam, px, py, pix)) {
+            float3 o, d;
+            camera_ray(cam, px, py, o, d);
+            float C0, C1, C2, T, depth;
+            int64_t last_key;
+            int count;
+            trace_forward<K, COUNT>(A.rec, A.nodes, A.P, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
+            A.rgb[3 * pix + 0] = fmaf(T, A.P.bg[0], C0);
+            A.rgb[3 * pix + 1] = fmaf(T, A.P.bg[1], C1);
+            A.rgb[3 * pix + 2] = fmaf(T, A.P.bg[2], C2);
+            A.alpha[pix] = 1.f - T;
+            if (A.depth) A.depth[pix] = depth;
+            A.sT[pix] = T;
+            A.skey[pix] = last_key;
+            A.sn[pix] = count;
+            if (COUNT) ++rays;
+        }
+        if (!PERSIST) break;
+    }
+    if (COUNT) {
+        unsigned long long v[6] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) atomicAdd(A.stats + k, v[k]);
+        }
+    }
+}
+
+template <int K, bool PERSIST, bool COUNT>
+__global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
+    const int lane = threadIdx.x & 31;
+    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Counters cnt;
+    uint32_t rays = 0;
+    while (true) {
+        if (PERSIST) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(A.queue + 1, 1ull);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (tile >= A.total_tiles) break;
+        DevCam cam;
+        int px, py;
+        int64_t pix;
+        if (tile_pixel(A, tile, lane, cam, px, py, pix)) {
+            const int n = A.sn[pix];
+            if (n > 0) {
+                float3 o, d;
+                camera_ray(cam, px, py, o, d);
+                const float gC[3] = {B.d_rgb[3 * pix], B.d_rgb[3 * pix + 1], B.d_rgb[3 * pix + 2]};
+                const float gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
+                trace_backward<K, COUNT>(A.rec, A.nodes, A.P, o, d, A.sT[pix], A.skey[pix], n, gC, gA, B.gtmp, cnt,
+                                         A.err);
+                if (COUNT) ++rays;
+            }
+        }
+        if (!PERSIST) break;
+    }
+    if (COUNT) {
+        unsigned long long v[6] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) atomicAdd(A.stats + k, v[k]);
+        }
+    }
+}
+
+// dL/dM, dL/dm, dL/dopacity, dL/drgb (Morton order) -> caller's gradients (Gaussian ids).
+// M = S^-1 R^T:  dL/ds_k = -(1/s_k) sum_l G[k][l] M[k][l];  dL/dR[l][k] = G[k][l] / s_k;
+// R = I + s_q K(q), s_q = 2/|q|^2 (App. A.6):  dR/dq_x = -s_q^2 q_x K + s_q dK/dq_x.
+__global__ void k_finalize(const float4* __restrict__ gtmp, const float4* __restrict__ rec,
+                           const uint32_t* __restrict__ perm, const float* __restrict__ quats,
+                           const float* __restrict__ scales, int64_t n, rs_gaussian_grads out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i = perm[j];
+    const float4 G0 = gtmp[4 * j], G1 = gtmp[4 * j + 1], G2 = gtmp[4 * j + 2], G3 = gtmp[4 * j + 3];
+    if (out.d_means) {
+        out.d_means[3 * i] += G0.w;
+        out.d_means[3 * i + 1] += G1.w;
+        out.d_means[3 * i + 2] += G2.w;
+    }
+    if (out.d_opacities) out.d_opacities[i] += G3.x;
+    if (out.d_rgb) {
+        out.d_rgb[3 * i] += G3.y;
+        out.d_rgb[3 * i + 1] += G3.z;
+        out.d_rgb[3 * i + 2] += G3.w;
+    }
+    if (!out.d_scales && !out.d_quats) return;
+    const float GM[3][3] = {{G0.x, G0.y, G0.z}, {G1.x, G1.y, G1.z}, {G2.x, G2.y, G2.z}};
+    const float4 m0 = rec[4 * j], m1 = rec[4 * j + 1], m2 = rec[4 * j + 2];
+    const float M[3][3] = {{m0.x, m0.y, m0.z}, {m1.x, m1.y, m1.z}, {m2.x, m2.y, m2.z}};
+    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    if (out.d_scales) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out.d_scales[3 * i + k] += -(GM[k][0] * M[k][0] + GM[k][1] * M[k][1] + GM[k][2] * M[k][2]) / s[k];
+    }
+    if (out.d_quats) {
+        const float qa = quats[4 * i], qb = quats[4 * i + 1], qc = quats[4 * i + 2], qd = quats[4 * i + 3];
+        const float sq = 2.f / (qa * qa + qb * qb + qc * qc + qd * qd);
+        float GR[3][3];  // dL/dR[l][k]
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) GR[l][k] = GM[k][l] / s[k];
+        const float Kq[3][3] = {{-(qc * qc + qd * qd), qb * qc - qa * qd, qb * qd + qa * qc},
+                                {qb * qc + qa * qd, -(qb * qb + qd * qd), qc * qd - qa * qb},
+                                {qb * qd - qa * qc, qc * qd + qa * qb, -(qb * qb + qc * qc)}};
+        float GK = 0.f;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) GK += GR[l][k] * Kq[l][k];
+        // sum over entries of GR (.) dK/dq_x
+        const float da = GR[0][1] * (-qd) + GR[0][2] * qc + GR[1][0] * qd + GR[1][2] * (-qb) + GR[2][0] * (-qc) +
+                         GR[2][1] * qb;
+        const float db = GR[0][1] * qc + GR[0][2] * qd + GR[1][0] * qc + GR[1][1] * (-2.f * qb) + GR[1][2] * (-qa) +
+                         GR[2][0] * qd + GR[2][1] * qa + GR[2][2] * (-2.f * qb);
+        const float dc = GR[0][0] * (-2.f * qc) + GR[0][1] * qb + GR[0][2] * qa + GR[1][0] * qb + GR[1][2] * qd +
+                         GR[2][0] * (-qa) + GR[2][1] * qd + GR[2][2] * (-2.f * qc);
+        const float dd = GR[0][0] * (-2.f * qd) + GR[0][1] * (-qa) + GR[0][2] * qb + GR[1][0] * qa +
+                         GR[1][1] * (-2.f * qd) + GR[1][2] * qc + GR[2][0] * qb + GR[2][1] * qc;
+        const float ns = -sq * sq * GK;
+        out.d_quats[4 * i] += ns * qa + sq * da;
+        out.d_quats[4 * i + 1] += ns * qb + sq * db;
+        out.d_quats[4 * i + 2] += ns * qc + sq * dc;
+        out.d_quats[4 * i + 3] += ns * qd + sq * dd;
+    }
+}
+
+__global__ void k_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px, const int32_t* py,
+                             float* o, float* d) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float3 oo, dd;
+    camera_ray(cams[ci[r]], px[r], py[r], oo, dd);
+    o[3 * r] = oo.x; o[3 * r + 1] = oo.y; o[3 * r + 2] = oo.z;
+    d[3 * r] = dd.x; d[3 * r + 1] = dd.y; d[3 * r + 2] = dd.z;
+}
+
+__global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs, const float* ro, const float* rd,
+                             const int32_t* sj, float Q, float t_near, float* out) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_pairs) return;
+    const int j = sj[k];
+    if (j < 0 || j >= n_gauss) {  // out-of-range id: report NaN instead of reading
+        out[4 * k] = out[4 * k + 1] = out[4 * k + 2] = out[4 * k + 3] = __int_as_float(0x7fc00000);
+        return;
+    }
+    Hit h;
+    ray_ellipsoid<false>(make_float3(ro[3 * k], ro[3 * k + 1], ro[3 * k + 2]),
+                         make_float3(rd[3 * k], rd[3 * k + 1], rd[3 * k + 2]), rec[4 * j], rec[4 * j + 1],
+                         rec[4 * j + 2], Q, t_near, h);
+    out[4 * k] = h.D2;
+    out[4 * k + 1] = h.t1;
+    out[4 * k + 2] = h.hit ? 1.f : 0.f;
+    out[4 * k + 3] = response_alpha(rec[4 * j + 3].x, h.D2);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------------
+template <int K, bool PERSIST, bool COUNT>
+static cudaError_t launch_fwd_k(const FwdArgs& A, int grid, int block, cudaStream_t st) {
+    k_render_fwd<K, PERSIST, COUNT><<<grid, block, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+template <int K, bool PERSIST>
+static int occupancy_fwd(int block, bool count) {
+    int nb = 0;
+    if (count)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, true>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, false>, block, 0);
+    return nb;
+}
+
+template <int K, bool PERSIST>
+static int occupancy_bwd(int block, bool count) {
+    int nb = 0;
+    if (count)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, true>, block, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, false>, block, 0);
+    return nb;
+}
+
+int persistent_grid(bool backward, int K, int block, bool count, int sms) {
+    int nb = 1;
+    if (!backward) {
+        if (K == 8) nb = occupancy_fwd<8, true>(block, count);
+        else if (K == 16) nb = occupancy_fwd<16, true>(block, count);
+        else nb = occupancy_fwd<32, true>(block, count);
+    } else {
+        if (K == 8) nb = occupancy_bwd<8, true>(block, count);
+        else if (K == 16) nb = occupancy_bwd<16, true>(block, count);
+        else nb = occupancy_bwd<32, true>(block, count);
+    }
+    return std::max(1, nb) * sms;
+}
+
+cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int grid, int block, cudaStream_t st) {
+#define RS_FWD(KK)                                                                   \
+    if (K == KK) {                                                                   \
+        if (persistent) return count ? launch_fwd_k<KK, true, true>(A, grid, block, st)   \
+                                     : launch_fwd_k<KK, true, false>(A, grid, block, st); \
+        return count ? launch_fwd_k<KK, false, true>(A, grid, block, st)                  \
+                     : launch_fwd_k<KK, false, false>(A, grid, block, st);                \
+    }
+    RS_FWD(8)
+    RS_FWD(16)
+    RS_FWD(32)
+#undef RS_FWD
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int grid,
+                            int block, cudaStream_t st) {
+#define RS_BWD(KK)                                                                                   \
+    if (K == KK) {                                                                                   \
+        if (persistent) {                                                                            \
+            if (count) k_render_bwd<KK, true, true><<<grid, block, 0, st>>>(A, B);                    \
+            else k_render_bwd<KK, true, false><<<grid, block, 0, st>>>(A, B);                         \
+        } else {                                                                                     \
+            if (count) k_render_bwd<KK, false, true><<<grid, block, 0, st>>>(A, B);                   \
+            else k_render_bwd<KK, false, false><<<grid, block, 0, st>>>(A, B);                        \
+        }                                                                                            \
+        return cudaGetLastError();                                                                   \
+    }
+    RS_BWD(8)
+    RS_BWD(16)
+    RS_BWD(32)
+#undef RS_BWD
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,
+                            const float* scales, int64_t n, const rs_gaussian_grads& out, cudaStream_t st) {
+    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gtmp, rec, perm, quats, scales, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px, const int32_t* py,
+                              float* o, float* d, cudaStream_t st) {
+    k_debug_rays<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cams, n, ci, px, py, o, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_hits(const float4* rec, int64_t n_gauss, int64_t n, const float* ro, const float* rd,
+                              const int32_t* sj, float Q, float t_near, float* out, cudaStream_t st) {
+    k_debug_hits<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(rec, n_gauss, n, ro, rd, sj, Q, t_near, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

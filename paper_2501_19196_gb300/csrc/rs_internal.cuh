@@ -1,0 +1,174 @@
+// rs_internal.cuh -- device data layout and the ray / ellipsoid arithmetic shared by the
+// render and adjoint kernels (RaySplats, arXiv 2501.19196).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/raysplats.h"
+
+namespace rs {
+
+// ---------------------------------------------------------------------------------------------
+// Layout in HBM
+//   rec[4 j + 0..2] = (M row k, mean_k)   M = S^-1 R^T (Prop. 1/2), rows k = 0, 1, 2
+//   rec[4 j + 3]    = (opacity, r, g, b)
+// j is the Gaussian's position in Morton order (sorted), so the 64 B records of one BVH leaf
+// are contiguous and sector aligned.  perm[j] maps back to the caller's Gaussian id.
+//   nodes[4 p + 0] = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   nodes[4 p + 1] = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   nodes[4 p + 2] = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   nodes[4 p + 3] = int (ref0, ref1, count0, count1)
+// ref >= 0 is an internal node; ref < 0 is a leaf holding Gaussians [~ref, ~ref + count).
+// ---------------------------------------------------------------------------------------------
+
+constexpr int kStackSize = 96;         // >= depth of a radix tree over 64-bit codes + 32-bit ids
+constexpr int64_t kEmptyKey = INT64_MAX;  // empty slot of an ascending k-buffer
+constexpr int64_t kEmptyKeyDesc = -1;     // empty slot of a descending k-buffer
+
+// device error word bits
+enum : int {
+    kErrReplayMismatch = 1,  // backward found a different number of hits than the forward
+    kErrBadScene = 2,        // non-finite or non-positive scale / zero quaternion seen in prep
+    kErrStack = 4,           // traversal stack overflow (cannot happen for kStackSize >= depth)
+    kErrLoopGuard = 8        // a traversal / round / refit loop exceeded its bound (corrupt tree)
+};
+
+struct DevCam {
+    float R[9];
+    float pos[3];
+    float fx, fy, cx, cy;
+    int32_t W, H, tiles_x, tiles_y;
+    int64_t tile_base;  // first global tile id of this camera
+    int64_t pix_base;   // first output pixel of this camera
+};
+
+struct TraceParams {
+    float Q, eps1, t_near;
+    float bg[3];
+    int32_t k_max;
+    int32_t max_rounds;    // guard: no ray needs more rounds than n / K + 2
+    int32_t max_visits;    // guard: a round visits each of the < n nodes at most once
+};
+
+// (t1, sorted id) packed into one ordered 64-bit key; t1 >= 0 so its bit pattern orders as
+// an unsigned integer.
+__device__ __forceinline__ int64_t pack_key(float t, int j) {
+    return (int64_t)(((uint64_t)__float_as_uint(t) << 32) | (uint32_t)j);
+}
+__device__ __forceinline__ float key_t(int64_t k) { return __uint_as_float((uint32_t)((uint64_t)k >> 32)); }
+__device__ __forceinline__ int key_j(int64_t k) { return (int)(uint32_t)((uint64_t)k & 0xffffffffu); }
+
+// ---------------------------------------------------------------------------------------------
+// Camera ray (a7): the fixed FP32 sequence of the ABI (no contraction: explicit _rn ops).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void camera_ray(const DevCam& c, int px, int py, float3& o, float3& d) {
+    const float x = __fdiv_rn(__fsub_rn(__fadd_rn((float)px, 0.5f), c.cx), c.fx);
+    const float y = __fdiv_rn(__fsub_rn(__fadd_rn((float)py, 0.5f), c.cy), c.fy);
+    float w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        w[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[3 * k], x), __fmul_rn(c.R[3 * k + 1], y)), c.R[3 * k + 2]);
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(w[0], w[0]), __fmul_rn(w[1], w[1])), __fmul_rn(w[2], w[2]));
+    const float n = __fsqrt_rn(n2);
+    d = make_float3(__fdiv_rn(w[0], n), __fdiv_rn(w[1], n), __fdiv_rn(w[2], n));
+    o = make_float3(c.pos[0], c.pos[1], c.pos[2]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Ray / confidence-ellipsoid solve (Prop. 1, Prop. 2) in FP32, numerically stable form.
+//
+// The ray is first re-centred at the point x_c = o + tc d nearest to the mean (tc = <m - o, d>)
+// so that the whitened origin o'' = M (x_c - m) is small; w = x_c - m is formed with
+// error-free transformations (TwoSum of o - m, TwoProduct of tc d), so it carries no rounding
+// of |o - m|-sized numbers.  Then, as in Prop. 1/2 with o' -> o'':
+//   d' = M d, a = <d', d'>, b = <o'', d'>, tm = -b / a,
+//   p = o'' + tm d'  (= M v, v = x_c + tm d - m),  D2 = <p, p>,
+//   t* = (-b - sgn(b) sqrt(a (Q - D2))) / a, t1'' = t* if b >= 0 else (<o'',o''> - Q) / (a t*),
+//   t1 = tc + t1''.
+// D2 and t1 do not depend on the choice of tc (a shift along the ray).  Every operation is an
+// explicit round-to-nearest intrinsic, so the forward and the adjoint kernels evaluate the
+// same bits.
+// ---------------------------------------------------------------------------------------------
+struct Hit {
+    float D2, t1;
+    bool hit;
+    float p[3];  // M-space closest-approach vector
+    float v[3];  // world vector from the mean to the point of maximum response
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <bool WANT_GEOM>
+__device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, const float4 r0,
+                                              const float4 r1, const float4 r2, float Q,
+                                              float t_near, Hit& h) {
+    const float m[3] = {r0.w, r1.w, r2.w};
+    const float oo[3] = {o.x, o.y, o.z};
+    const float dd[3] = {d.x, d.y, d.z};
+    // tc = <m - o, d>
+    float tc = 0.f;
+    float e_hi[3], e_lo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        two_sum(oo[k], -m[k], e_hi[k], e_lo[k]);  // o - m exactly as e_hi + e_lo
+        tc = __fmaf_rn(-e_hi[k], dd[k], tc);
+    }
+    // w = (o - m) + tc d, exactly up to one final rounding per component
+    float w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float ph = __fmul_rn(tc, dd[k]);
+        const float pl = __fmaf_rn(tc, dd[k], -ph);
+        w[k] = __fadd_rn(__fadd_rn(e_hi[k], ph), __fadd_rn(e_lo[k], pl));
+    }
+    const float Mr[3][3] = {{r0.x, r0.y, r0.z}, {r1.x, r1.y, r1.z}, {r2.x, r2.y, r2.z}};
+    float op[3], dp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        op[k] = __fmaf_rn(Mr[k][2], w[2], __fmaf_rn(Mr[k][1], w[1], __fmul_rn(Mr[k][0], w[0])));
+        dp[k] = __fmaf_rn(Mr[k][2], dd[2], __fmaf_rn(Mr[k][1], dd[1], __fmul_rn(Mr[k][0], dd[0])));
+    }
+    const float a = __fmaf_rn(dp[2], dp[2], __fmaf_rn(dp[1], dp[1], __fmul_rn(dp[0], dp[0])));
+    const float b = __fmaf_rn(op[2], dp[2], __fmaf_rn(op[1], dp[1], __fmul_rn(op[0], dp[0])));
+    const float tm = -__fdiv_rn(b, a);
+    float p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = __fmaf_rn(tm, dp[k], op[k]);
+    const float D2 = __fmaf_rn(p[2], p[2], __fmaf_rn(p[1], p[1], __fmul_rn(p[0], p[0])));
+    h.D2 = D2;
+    h.hit = false;
+    h.t1 = 0.f;
+    if (D2 <= Q) {
+        const float root = __fsqrt_rn(__fmul_rn(a, __fsub_rn(Q, D2)));
+        float t1r;
+        if (b >= 0.f) {
+            t1r = __fdiv_rn(__fsub_rn(-b, root), a);
+        } else {
+            const float tstar = __fdiv_rn(__fadd_rn(-b, root), a);
+            const float c = __fsub_rn(__fmaf_rn(op[2], op[2], __fmaf_rn(op[1], op[1], __fmul_rn(op[0], op[0]))), Q);
+            t1r = __fdiv_rn(c, __fmul_rn(a, tstar));
+        }
+        const float t1 = __fadd_rn(__fadd_rn(tc, t1r), 0.0f);  // +0 turns -0 into +0
+        h.t1 = t1;
+        h.hit = t1 >= t_near;
+    }
+    if (WANT_GEOM) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            h.p[k] = p[k];
+            h.v[k] = __fmaf_rn(tm, dd[k], w[k]);
+        }
+    }
+}
+
+// alpha_i = opacity * exp(-D2 / 2)  (Eq. 8, Prop. 2)
+__device__ __forceinline__ float response_alpha(float opacity, float D2) {
+    return __fmul_rn(opacity, expf(__fmul_rn(-0.5f, D2)));
+}
+
+}  // namespace rs

@@ -1,0 +1,74 @@
+// rs_render.h -- kernel argument blocks and launchers of render.cu (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rs_internal.cuh"
+
+namespace rs {
+
+struct FwdArgs {
+    const float4* rec;
+    const float4* nodes;
+    const DevCam* cams;
+    int n_cams;
+    int cam_single;       // >= 0: plain launch of this camera only; -1: persistent over all
+    int64_t total_tiles;  // tiles of the launch (one camera, or all cameras)
+    int tile_w;           // tile_h = 32 / tile_w
+    TraceParams P;
+    float* rgb;
+    float* alpha;
+    float* depth;
+    float* sT;        // per pixel: final transmittance
+    int64_t* skey;    // per pixel: (t1, sorted id) key of the last composited hit
+    int* sn;          // per pixel: composited hits
+    unsigned long long* queue;  // [0] forward tile counter, [1] backward tile counter
+    int* err;
+    unsigned long long* stats;
+};
+
+struct BwdArgs {
+    const float* d_rgb;
+    const float* d_alpha;
+    float4* gtmp;  // 4 per Gaussian (Morton order): (dM row k, dm_k) k = 0..2, (dop, drgb)
+};
+
+int persistent_grid(bool backward, int K, int block, bool count, int sms);
+cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int grid, int block,
+                           cudaStream_t st);
+cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int grid,
+                            int block, cudaStream_t st);
+cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,
+                            const float* scales, int64_t n, const rs_gaussian_grads& out, cudaStream_t st);
+cudaError_t launch_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px,
+                              const int32_t* py, float* o, float* d, cudaStream_t st);
+cudaError_t launch_debug_hits(const float4* rec, int64_t n_gauss, int64_t n, const float* ro, const float* rd,
+                              const int32_t* sj, float Q, float t_near, float* out, cudaStream_t st);
+
+}  // namespace rs
+
+struct rs_fwd_state {
+    int device = 0;
+    int64_t n_pix = 0, cap_pix = 0;
+    int64_t cap_gauss = 0;
+    int n_cams = 0, cap_cams = 0;
+    std::vector<rs::DevCam> cams_host;  // last uploaded table
+    rs::DevCam* cams_dev = nullptr;
+    rs::DevCam* cams_pinned = nullptr;  // staging for the upload
+    float* sT = nullptr;
+    int64_t* skey = nullptr;
+    int* sn = nullptr;
+    float4* gtmp = nullptr;
+    unsigned long long* queue = nullptr;
+    int* err = nullptr;
+    // what the forward recorded
+    rs::TraceParams P{};
+    int64_t total_tiles = 0;
+    int tile_w = 8, kbuf = 16, block_warps = 4;
+    int persistent = 1;
+    const rs_accel* accel = nullptr;
+    int64_t n_gauss = 0;
+};

@@ -1,0 +1,122 @@
+"""GPU parity of the adjoint (reverse replay, float4 atomics, finalize) against the oracle's
+FP64 gradient, through the C ABI and through the torch.autograd.Function.  Tolerance: 1e-3
+relative L2 per gradient array.  Rays where FP32 and FP64 may take a different discrete
+decision (any oracle decision flag) get a zero upstream gradient on both sides."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_util import TOL_GRAD, gpu_render, oracle_pixels, params, pixel_index, rel_l2, to_dev
+from workloads import scenes
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("means", "quats", "scales", "opacities", "rgb")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _grad_case(sc, cams, prm, tune=None, stride=1, seed=1, with_alpha=True):
+    from paper_2501_19196_gb300 import native
+    cam, px, py = scenes.pixel_grid(cams, stride=stride)
+    idx = pixel_index(cams, cam, px, py)
+    P = int(cams.n_pixels().sum())
+    rng = np.random.default_rng(seed)
+    gc_s = rng.standard_normal((len(cam), 3))
+    ga_s = rng.standard_normal(len(cam)) if with_alpha else np.zeros(len(cam))
+    ora0 = oracle_pixels(sc, cams, cam, px, py, prm)
+    bad = (ora0["mask"] & oracle.AMB_DECISION) != 0
+    gc_s[bad] = 0.0
+    ga_s[bad] = 0.0
+    ora = oracle_pixels(sc, cams, cam, px, py, prm, dl_rgb=gc_s, dl_alpha=ga_s)
+    # full-frame upstream gradient: zero except at the listed pixels
+    gc = np.zeros((P, 3), np.float32)
+    ga = np.zeros(P, np.float32)
+    gc[idx] = gc_s
+    ga[idx] = ga_s
+    out, r, dev = gpu_render(sc, cams, prm, tune=tune or native.default_tune(), keep=True)
+    grads = r.backward(torch.from_numpy(gc).cuda(), torch.from_numpy(ga).cuda())
+    torch.cuda.synchronize()
+    r.check_device()
+    r.close()
+    errs = {k: rel_l2(grads[k].cpu().numpy().astype(np.float64).reshape(ora["grads"][k].shape), ora["grads"][k])
+            for k in KEYS}
+    return errs, bad.mean()
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_gradients_tiny_scenes(seed):
+    sc = scenes.random_tiny_scene(300 + seed, n=40, flat_frac=0.3 if seed % 2 else 0.0)
+    cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 21, 17, 55.0),
+                                  scenes.look_at_camera((-3.0, 0.5, 0.7), (0.1, 0, 0), 16, 16, 45.0)])
+    for kw in (dict(), dict(eps1=0.2), dict(k_max=2), dict(background=(0.3, 0.2, 1.0))):
+        errs, bad = _grad_case(sc, cams, params(**kw), seed=seed)
+        assert max(errs.values()) < TOL_GRAD, (kw, errs)
+
+
+def test_gradients_workload_1k_full_frame():
+    wl = scenes.workload(1)
+    errs, bad = _grad_case(wl.scene, wl.cams, params(eps1=wl.eps1, background=wl.background))
+    print("1k/64x64 gradient rel-L2:", {k: f"{v:.2e}" for k, v in errs.items()}, f"decision-flagged {bad:.4f}")
+    assert max(errs.values()) < TOL_GRAD, errs
+
+
+def test_gradients_shell_200k_sampled_pixels():
+    wl = scenes.workload(2)
+    errs, bad = _grad_case(wl.scene, wl.cams, params(eps1=wl.eps1, background=wl.background), stride=23)
+    print("200k sampled gradient rel-L2:", {k: f"{v:.2e}" for k, v in errs.items()}, f"flagged {bad:.4f}")
+    assert max(errs.values()) < TOL_GRAD, errs
+
+
+def test_gradients_invariant_to_tunables():
+    from paper_2501_19196_gb300 import native
+    sc = scenes.random_tiny_scene(77, n=300, spread=1.0, log_mu=-2.5)
+    cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 40, 24, 55.0),
+                                  scenes.look_at_camera((2.0, 2.0, -2.0), (0, 0, 0), 16, 40, 50.0)])
+    prm = params(eps1=1e-3)
+    for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16)):
+        errs, _ = _grad_case(sc, cams, prm, tune=native.default_tune(**kw))
+        assert max(errs.values()) < TOL_GRAD, (kw, errs)
+
+
+def test_autograd_function_matches_direct_backward():
+    from paper_2501_19196_gb300 import Renderer, render_gaussians
+    sc = scenes.random_tiny_scene(9, n=80, flat_frac=0.2)
+    cams = scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 24, 20, 55.0)
+    prm = params(background=(0.1, 0.2, 0.3))
+    leaves = [t.clone().requires_grad_(True) for t in to_dev(sc)]
+    rgb, alpha, depth = render_gaussians(*leaves, cams, prm)
+    rng = np.random.default_rng(0)
+    w = torch.from_numpy(rng.standard_normal((rgb.shape[0], 3)).astype(np.float32)).cuda()
+    wa = torch.from_numpy(rng.standard_normal(rgb.shape[0]).astype(np.float32)).cuda()
+    loss = (rgb * w).sum() + (alpha * wa).sum()
+    loss.backward()
+    r = Renderer()
+    r.build(*to_dev(sc))
+    r.render(cams, prm)
+    ref = r.backward(w.contiguous(), wa.contiguous())
+    torch.cuda.synchronize()
+    for leaf, k in zip(leaves, KEYS):
+        np.testing.assert_allclose(leaf.grad.cpu().numpy().reshape(-1), ref[k].cpu().numpy().reshape(-1),
+                                   rtol=1e-5, atol=1e-6)
+    r.close()
+
+
+def test_gradient_through_log_scale_and_logit_activations():
+    """The ABI is physical; activations (exp for log-scales, sigmoid for opacity logits) are
+    chained by torch autograd on top."""
+    from paper_2501_19196_gb300 import render_gaussians
+    sc = scenes.random_tiny_scene(11, n=50)
+    cams = scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 16, 16, 55.0)
+    m, q, s, o, c = to_dev(sc)
+    log_s = torch.log(s).requires_grad_(True)
+    logit = torch.logit(o).requires_grad_(True)
+    rgb, alpha, _ = render_gaussians(m, q, torch.exp(log_s), torch.sigmoid(logit), c, cams, params())
+    (rgb.sum() + alpha.sum()).backward()
+    assert torch.isfinite(log_s.grad).all() and torch.isfinite(logit.grad).all()
+    assert log_s.grad.abs().sum() > 0 and logit.grad.abs().sum() > 0
