@@ -24,6 +24,7 @@ _LIB = None
 
 AMB_BOUNDARY, AMB_TIE, AMB_EPS1, AMB_TNEAR, AMB_IMPACT = 1, 2, 4, 8, 16
 AMB_DECISION = AMB_BOUNDARY | AMB_TIE | AMB_EPS1 | AMB_TNEAR
+IMP_BOUNDARY, IMP_TIE, IMP_EPS1 = 32, 64, 128
 
 
 class OrParams(ctypes.Structure):
@@ -50,7 +51,7 @@ def lib():
         L.or_quat_to_rot.restype = None
         L.or_quat_to_rot.argtypes = [P, P]
         L.or_morton.restype = None
-        L.or_morton.argtypes = [i64, P, i32, P, P]
+        L.or_morton.argtypes = [i64, P, P, i32, P, P]
         L.or_sort_perm.restype = ctypes.c_int
         L.or_sort_perm.argtypes = [i64, P, P, P]
         L.or_radix_tree.restype = ctypes.c_int
@@ -154,12 +155,16 @@ def render(scene, cams, ray_cam, px, py, Q, eps1=1e-4, k_max=2 ** 31 - 1, backgr
     return render_rays(scene, o, d, Q, eps1, k_max, background, t_near, dl_rgb, dl_alpha, threads)
 
 
-def morton(means, bits):
+def morton(means, bits, scales=None):
+    """Morton codes (bits = 10, 21) or extended codes with a size class (bits = 20, needs scales)."""
     means = _c(means, np.float32)
     n = means.shape[0]
     codes = np.zeros(n, np.uint64)
     lohi = np.zeros(6, np.float32)
-    lib().or_morton(n, _p(means), int(bits), _p(codes), _p(lohi))
+    sc = None if scales is None else _c(scales, np.float32)
+    if bits == 20 and sc is None:
+        raise ValueError("extended codes need the scales")
+    lib().or_morton(n, _p(means), _p(sc), int(bits), _p(codes), _p(lohi))
     return codes, lohi
 
 

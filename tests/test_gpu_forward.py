@@ -52,7 +52,7 @@ def _export(scene, **tune):
     return ex
 
 
-@pytest.mark.parametrize("bits", [10, 21])
+@pytest.mark.parametrize("bits", [10, 20, 21])
 @pytest.mark.parametrize("which", ["cube1k", "dups", "clusters"])
 def test_morton_codes_and_order_bit_exact(bits, which):
     if which == "cube1k":
@@ -63,14 +63,14 @@ def test_morton_codes_and_order_bit_exact(bits, which):
     else:
         sc = scenes.scene_unbounded(200_000, seed=3)
     ex = _export(sc, morton_bits=bits)
-    codes, lohi = oracle.morton(sc.means, bits)
+    codes, lohi = oracle.morton(sc.means, bits, sc.scales)
     perm, sorted_codes = oracle.sort_perm(codes)
     np.testing.assert_array_equal(ex["lo_hi"], lohi)
     np.testing.assert_array_equal(ex["codes"], sorted_codes)
     np.testing.assert_array_equal(ex["perm"], perm)
 
 
-@pytest.mark.parametrize("n,bits", [(2, 21), (3, 21), (1000, 21), (40000, 10)])
+@pytest.mark.parametrize("n,bits", [(2, 21), (3, 21), (1000, 21), (40000, 10), (20000, 20)])
 def test_radix_tree_matches_definition(n, bits):
     sc = scenes.random_tiny_scene(n, n=n, spread=2.0)
     ex = _export(sc, morton_bits=bits)
@@ -140,15 +140,16 @@ def test_hit_test_numerics_against_fp64():
     for t in range(k):
         D2[t], t1[t], hit[t], _ = oracle.ray_gaussian(o[t], d[t], sc.means[gi[t]], sc.quats[gi[t]],
                                                       sc.scales[gi[t]], Q)
-    clear = np.abs(D2 - Q) > 1e-4 * Q
+    clear = np.abs(D2 - Q) > 2e-5 * Q   # the oracle's boundary band
     assert np.mean(hit) > 0.2
     assert np.all((out[clear, 2] > 0.5) == hit[clear])
     both = clear & hit
     errD = np.abs(out[both, 0] - D2[both]) / np.maximum(1.0, D2[both])
     errt = np.abs(out[both, 1] - t1[both]) / np.maximum(1.0, np.abs(t1[both]))
     print(f"hit numerics: max |dD2|/max(1,D2) = {errD.max():.3e}, max |dt1|/max(1,t1) = {errt.max():.3e}")
-    assert errD.max() < 2e-5
-    assert errt.max() < 2e-6
+    # the oracle's ambiguity bands (2e-5 Q in D2, 5e-7 in t1) assume these bounds with margin
+    assert errD.max() < 1e-5
+    assert errt.max() < 2.5e-7
 
 
 # ------------------------------------------------------------------------------------------
@@ -225,6 +226,7 @@ def test_tunables_and_launch_modes_bit_identical():
     ref = gpu_render(sc, cams, prm, tune=native.default_tune())
     for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(leaf_size=8), dict(leaf_size=16),
                dict(tile_w=4), dict(tile_w=16), dict(tile_w=32), dict(persistent=0), dict(morton_bits=10),
+               dict(morton_bits=20),
                dict(block_warps=1), dict(block_warps=2)):
         out = gpu_render(sc, cams, prm, tune=native.default_tune(**kw))
         for k in ("rgb", "alpha", "depth"):

@@ -443,6 +443,30 @@ def test_morton_brute_force_interleave():
         np.testing.assert_array_equal(lohi, np.concatenate([lo, hi]))
 
 
+def test_extended_morton_size_class():
+    rng = np.random.default_rng(16)
+    means = rng.uniform(-3, 5, (400, 3)).astype(np.float32)
+    scales = np.exp(rng.normal(-4, 1.5, (400, 3))).astype(np.float32)
+    codes, _ = oracle.morton(means, 20, scales)
+    lo, hi = means.min(0), means.max(0)
+    ext = hi - lo
+    cell = np.clip(np.floor((means - lo) / ext * np.float32(2 ** 20)), 0, 2 ** 20 - 1).astype(np.int64)
+    _, e_ext = np.frexp(np.float32(ext.max()))
+    for i in range(0, 400, 3):
+        _, e_s = np.frexp(np.float32(scales[i].max()))           # frexp exponent = E - 126
+        cls = int(np.clip(e_s - e_ext + 11, 0, 7))
+        ref = 0
+        for b in range(19, 15, -1):
+            for k in range(3):
+                ref = (ref << 1) | int((cell[i, k] >> b) & 1)
+        ref = (ref << 3) | cls
+        for b in range(15, -1, -1):
+            for k in range(3):
+                ref = (ref << 1) | int((cell[i, k] >> b) & 1)
+        assert int(codes[i]) == ref
+    assert int(codes.max()) < 2 ** 63
+
+
 def test_sort_is_stable_by_code_then_index():
     rng = np.random.default_rng(7)
     codes = rng.integers(0, 50, 1000).astype(np.uint64)
