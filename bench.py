@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--kbuf", type=int, default=None)
     p.add_argument("--leaf", type=int, default=None)
     p.add_argument("--tile-w", type=int, default=None)
+    p.add_argument("--profile", action="store_true",
+                   help="ncu mode: `warmup` eager batched steps, then one more step, then exit (no JSON)")
     return p.parse_args()
 
 
@@ -287,6 +289,15 @@ def run_ours(args):
             ms = float(t.item())
         return ms, clocks
 
+    if args.profile:
+        for _ in range(args.warmup + 1):
+            step(rb)
+        torch.cuda.synchronize()
+        rb.check_device()
+        rb.close()
+        rp.close()
+        return
+
     # --- warm up both renderers eagerly (allocations happen here) ---
     step(rb)
     step(rp)
@@ -412,7 +423,7 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{nr} stratified rays of the same workload, fwd + gradient, FP64 brute force, {dt:.1f} s"}
 
-    launches_build = 3 + 3 * (8 if tune_b.morton_bits == 21 else 4) + 3
+    launches_build = 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3
     gpu_launches = args.steps * (launches_build + 1 + 2)
     value = P / ms_fb / 1e3 * world
     line = {

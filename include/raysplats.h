@@ -125,7 +125,9 @@ typedef struct {
  *   tile_w, tile_h  ray tile handled by one warp; tile_w * tile_h == 32
  *   kbuf            per-ray k-buffer depth: 8, 16 or 32
  *   leaf_size       BVH leaf size 1..16 (used by rs_build_accel)
- *   morton_bits     10 (30-bit codes) or 21 (63-bit codes) bits per axis
+ *   morton_bits     10 (30-bit codes) or 21 (63-bit codes) bits per axis, or 20: extended
+ *                   63-bit codes, 20 bits per axis plus a 3-bit size class (from the exponent
+ *                   of the largest scale) below the top four levels
  *   persistent      0: one launch per camera; 1: one persistent launch over all cameras'
  *                   ray tiles through a device work queue
  *   block_warps     warps per CTA: 1..16 */
@@ -203,6 +205,21 @@ rs_status rs_render_backward_counted(const rs_gaussians* g, const rs_accel* acce
                                      const rs_fwd_state* state, const rs_frame_grad* dl,
                                      const rs_tune_params* tune, rs_gaussian_grads* out,
                                      uint64_t* stats_device, void* cuda_stream);
+
+/* Autotuner (a11).  Times one training step (rs_build_accel + rs_render + optionally
+ * rs_render_backward) of the caller's scene and cameras for each of n_candidates tunables
+ * (1 untimed warm-up + `reps` steps timed with CUDA events on `cuda_stream`), writes the mean
+ * milliseconds per step of candidate k to ms_out[k] (host array, may be NULL) and the fastest
+ * candidate to *best.  scratch / scratch_grads / dl: caller's device buffers of the rs_render /
+ * rs_render_backward layouts, used as outputs of the timed steps (their contents are
+ * overwritten / accumulated into); dl == NULL times the forward only.  Allocates its own
+ * temporary accel and state and synchronises the stream.  A candidate that fails validation is
+ * skipped (ms_out = -1); RS_ERR_INVALID_ARG if none is valid. */
+rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int32_t n_cams,
+                  const rs_render_params* params, const rs_tune_params* candidates,
+                  int32_t n_candidates, int32_t reps, rs_frame* scratch,
+                  const rs_frame_grad* dl, rs_gaussian_grads* scratch_grads,
+                  rs_tune_params* best, float* ms_out, void* cuda_stream);
 
 /* Free a handle (NULL is accepted).  Synchronises the device before freeing. */
 rs_status rs_accel_destroy(rs_accel* accel);

@@ -60,8 +60,8 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
         return set_error(RS_ERR_INVALID_ARG, "kbuf %d: must be 8, 16 or 32", t->kbuf);
     if (build && (t->leaf_size < 1 || t->leaf_size > 16))
         return set_error(RS_ERR_INVALID_ARG, "leaf_size %d: must be 1..16", t->leaf_size);
-    if (build && t->morton_bits != 10 && t->morton_bits != 21)
-        return set_error(RS_ERR_INVALID_ARG, "morton_bits %d: must be 10 or 21", t->morton_bits);
+    if (build && t->morton_bits != 10 && t->morton_bits != 20 && t->morton_bits != 21)
+        return set_error(RS_ERR_INVALID_ARG, "morton_bits %d: must be 10, 20 (extended) or 21", t->morton_bits);
     if (t->block_warps < 1 || t->block_warps > 4)
         return set_error(RS_ERR_INVALID_ARG, "block_warps %d: must be 1..4", t->block_warps);
     return RS_OK;
@@ -506,6 +506,69 @@ rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray
     const cudaError_t e =
         launch_debug_hits(accel->rec, accel->n, n_pairs, ray_o, ray_d, sorted_j, Q, t_near, out, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "debug hits: %s", cudaGetErrorString(e));
+    return RS_OK;
+}
+
+rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int32_t n_cams,
+                  const rs_render_params* params, const rs_tune_params* candidates, int32_t n_candidates,
+                  int32_t reps, rs_frame* scratch, const rs_frame_grad* dl, rs_gaussian_grads* scratch_grads,
+                  rs_tune_params* best, float* ms_out, void* cuda_stream) {
+    g_err[0] = 0;
+    if (!candidates || n_candidates < 1 || reps < 1 || !best || !scratch)
+        return set_error(RS_ERR_INVALID_ARG, "rs_tune: need candidates, reps >= 1, best and scratch");
+    if (dl && !scratch_grads) return set_error(RS_ERR_INVALID_ARG, "rs_tune: dl given without scratch_grads");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_check("rs_tune event create");
+    }
+    float best_ms = -1.f;
+    rs_status last = RS_ERR_INVALID_ARG;
+    char first_err[512] = "";
+    for (int c = 0; c < n_candidates; ++c) {
+        const rs_tune_params& t = candidates[c];
+        rs_accel* A = nullptr;
+        rs_fwd_state* S = nullptr;
+        float ms = -1.f;
+        auto one = [&]() -> rs_status {
+            rs_status st = rs_build_accel(g, Q_box, &t, &A, cuda_stream);
+            if (st) return st;
+            if ((st = rs_render(g, A, cams, n_cams, params, &t, scratch, &S, cuda_stream))) return st;
+            if (dl) st = rs_render_backward(g, A, S, dl, &t, scratch_grads, cuda_stream);
+            return st;
+        };
+        rs_status st = one();  // warm-up (allocates)
+        if (!st) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && !st; ++r) st = one();
+            cudaEventRecord(e1, s);
+            if (!st && cudaEventSynchronize(e1) == cudaSuccess) {
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= (float)reps;
+                if (!st) st = rs_check_device(A, S, cuda_stream);
+            } else if (!st) {
+                st = cuda_check("rs_tune timing");
+            }
+        }
+        if (st) {
+            if (!first_err[0]) snprintf(first_err, sizeof(first_err), "candidate %d: %s", c, g_err);
+            last = st;
+            ms = -1.f;
+        }
+        cudaStreamSynchronize(s);
+        rs_state_destroy(S);
+        rs_accel_destroy(A);
+        if (ms_out) ms_out[c] = ms;
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            *best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_ms < 0.f) return set_error(last ? last : RS_ERR_INVALID_ARG, "rs_tune: no candidate ran (%s)", first_err);
+    g_err[0] = 0;
     return RS_OK;
 }
 

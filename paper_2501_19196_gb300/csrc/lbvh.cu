@@ -75,23 +75,42 @@ __device__ __forceinline__ uint64_t spread3(uint64_t x) {  // 21 bits -> every t
     return x;
 }
 
-__global__ void k_morton(const float* __restrict__ means, int64_t n, const unsigned* __restrict__ b,
-                         int bits, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// bits = 10 / 21: plain 30 / 63-bit codes.  bits = 20: extended 63-bit code
+// [x y z interleave of cell bits 19..16][3-bit size class][interleave of bits 15..0] with
+// class = clamp(E(max scale) - E(max scene extent) + 11, 0, 7), E = biased FP32 exponent, so
+// that large Gaussians gather in their own subtrees instead of inflating their neighbours'.
+__global__ void k_morton(const float* __restrict__ means, const float* __restrict__ scales, int64_t n,
+                         const unsigned* __restrict__ b, int bits, uint64_t* __restrict__ keys,
+                         uint32_t* __restrict__ vals) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float scale = (float)(1u << bits);
     const unsigned cmax = (1u << bits) - 1u;
     uint64_t cell[3];
+    float ext_max = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float lo = ord2f(b[k]), hi = ord2f(b[3 + k]);
         float ext = __fsub_rn(hi, lo);
         if (!(ext > 0.f)) ext = 1.f;
+        ext_max = fmaxf(ext_max, ext);
         const float u = __fdiv_rn(__fsub_rn(means[3 * i + k], lo), ext);
         const float f = floorf(__fmul_rn(u, scale));
         cell[k] = f <= 0.f ? 0u : (f >= (float)cmax ? cmax : (unsigned)f);
     }
-    keys[i] = (spread3(cell[0]) << 2) | (spread3(cell[1]) << 1) | spread3(cell[2]);
+    uint64_t code;
+    if (bits == 20) {
+        const uint64_t hi3 = (spread3(cell[0] >> 16) << 2) | (spread3(cell[1] >> 16) << 1) | spread3(cell[2] >> 16);
+        const uint64_t lo3 = (spread3(cell[0] & 0xffffu) << 2) | (spread3(cell[1] & 0xffffu) << 1) |
+                             spread3(cell[2] & 0xffffu);
+        const float smax = fmaxf(fmaxf(scales[3 * i], scales[3 * i + 1]), scales[3 * i + 2]);
+        int c = (int)((__float_as_uint(smax) >> 23) & 0xffu) - (int)((__float_as_uint(ext_max) >> 23) & 0xffu) + 11;
+        c = c < 0 ? 0 : (c > 7 ? 7 : c);
+        code = (hi3 << 51) | ((uint64_t)c << 48) | lo3;
+    } else {
+        code = (spread3(cell[0]) << 2) | (spread3(cell[1]) << 1) | spread3(cell[2]);
+    }
+    keys[i] = code;
     vals[i] = (uint32_t)i;
 }
 
@@ -386,9 +405,9 @@ rs_status build_accel_device(Accel& A, const rs_gaussians& g, const rs_tune_para
         const unsigned grid = (unsigned)std::min<int64_t>(grid_for(n, 256), 4 * 152);
         k_bounds<<<grid, 256, 0, st>>>(g.means, n, A.bounds);
     }
-    k_morton<<<grid_for(n, 256), 256, 0, st>>>(g.means, n, A.bounds, bits, A.keys[0], A.vals[0]);
+    k_morton<<<grid_for(n, 256), 256, 0, st>>>(g.means, g.scales, n, A.bounds, bits, A.keys[0], A.vals[0]);
     const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
-    const int passes = bits == 21 ? 8 : 4;
+    const int passes = bits == 10 ? 4 : 8;
     for (int ps = 0; ps < passes; ++ps) {
         const int src = ps & 1, dst = src ^ 1;
         k_sort_hist<<<nblocks, kSortThreads, 0, st>>>(A.keys[src], n, 8 * ps, A.hist, nblocks);

@@ -32,36 +32,31 @@ __device__ __forceinline__ float safe_rcp(float x) {
     return __frcp_rn(ax > 1e-30f ? x : copysignf(1e-30f, x));
 }
 
-// Both children's boxes against [tlo, thi]; the computed entry/exit are widened by 1e-6
-// relative so that rounding can never prune a box that holds a hit inside [tlo, thi].
+// Entry and exit parameters of both children's boxes, widened by 1e-6 relative so that rounding
+// can never drop a box that holds a hit (the boxes themselves are padded too).
 __device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const float4 n2, const float3 o,
-                                      const float3 inv, float tlo, float thi, bool& h0, bool& h1,
-                                      float& e0, float& e1) {
+                                      const float3 inv, float& en0, float& ex0, float& en1, float& ex1) {
     {
         const float a0 = (n0.x - o.x) * inv.x, b0 = (n0.y - o.x) * inv.x;
         const float a1 = (n0.z - o.y) * inv.y, b1 = (n0.w - o.y) * inv.y;
         const float a2 = (n2.x - o.z) * inv.z, b2 = (n2.y - o.z) * inv.z;
-        float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
-        float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
-        en = fmaf(-1e-6f, fabsf(en), en);
-        ex = fmaf(1e-6f, fabsf(ex), ex);
-        e0 = fmaxf(en, tlo);
-        h0 = e0 <= fminf(ex, thi);
+        const float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
+        const float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
+        en0 = fmaf(-1e-6f, fabsf(en), en);
+        ex0 = fmaf(1e-6f, fabsf(ex), ex);
     }
     {
         const float a0 = (n1.x - o.x) * inv.x, b0 = (n1.y - o.x) * inv.x;
         const float a1 = (n1.z - o.y) * inv.y, b1 = (n1.w - o.y) * inv.y;
         const float a2 = (n2.z - o.z) * inv.z, b2 = (n2.w - o.z) * inv.z;
-        float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
-        float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
-        en = fmaf(-1e-6f, fabsf(en), en);
-        ex = fmaf(1e-6f, fabsf(ex), ex);
-        e1 = fmaxf(en, tlo);
-        h1 = e1 <= fminf(ex, thi);
+        const float en = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
+        const float ex = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
+        en1 = fmaf(-1e-6f, fabsf(en), en);
+        ex1 = fmaf(1e-6f, fabsf(ex), ex);
     }
 }
 
-// ascending k-buffer: keys[0] nearest; insert `key` (< keys[K-1]) by one bubble pass
+// ascending buffer: keys[0] nearest; insert `key` (< keys[K-1]) by one bubble pass
 template <int K>
 __device__ __forceinline__ void kbuf_insert_asc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
     keys[K - 1] = key;
@@ -78,7 +73,7 @@ __device__ __forceinline__ void kbuf_insert_asc(int64_t (&keys)[K], float (&d2)[
     }
 }
 
-// descending k-buffer: keys[0] farthest; insert `key` (> keys[K-1])
+// descending buffer: keys[0] farthest; insert `key` (> keys[K-1])
 template <int K>
 __device__ __forceinline__ void kbuf_insert_desc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
     keys[K - 1] = key;
@@ -95,121 +90,33 @@ __device__ __forceinline__ void kbuf_insert_desc(int64_t (&keys)[K], float (&d2)
     }
 }
 
+// drop keys[0] (the hit just composited / replayed)
+template <int K>
+__device__ __forceinline__ void kbuf_pop_front(int64_t (&keys)[K], float (&d2)[K], int64_t empty) {
+#pragma unroll
+    for (int s = 0; s < K - 1; ++s) {
+        keys[s] = keys[s + 1];
+        d2[s] = d2[s + 1];
+    }
+    keys[K - 1] = empty;
+}
+
 struct Counters {
     uint32_t nodes = 0, tests = 0, hits = 0, rounds = 0, inserted = 0;
 };
 
-// One traversal round.  DESC = false: collect the K smallest keys > lo_key.  DESC = true:
-// collect the K largest keys < hi_key.  Pruning: box entry <= the t of the K-th kept key (or
-// of hi_key), box exit >= the t of lo_key (or of the K-th kept key).
-template <int K, bool DESC, bool COUNT>
-__device__ __forceinline__ void traverse_round(const float4* __restrict__ rec, const float4* __restrict__ nodes,
-                                               const TraceParams& P, const float3 o, const float3 d,
-                                               const float3 inv, int64_t bound_key, int64_t (&keys)[K],
-                                               float (&d2)[K], Counters& cnt, int* err) {
-    int stack[kStackSize];
-    float stack_t[kStackSize];
-    int sp = 0;
-    int node = 0;
-    const float t_bound = DESC ? key_t(bound_key) : (bound_key < 0 ? P.t_near : key_t(bound_key));
-    int visits = 0;
-    while (true) {
-        if (++visits > P.max_visits) {
-            atomicOr(err, kErrLoopGuard);
-            break;
-        }
-        const float4 n0 = __ldg(nodes + 4 * node + 0);
-        const float4 n1 = __ldg(nodes + 4 * node + 1);
-        const float4 n2 = __ldg(nodes + 4 * node + 2);
-        const float4 n3 = __ldg(nodes + 4 * node + 3);
-        if (COUNT) cnt.nodes++;
-        float tlo, thi;
-        if (!DESC) {
-            tlo = t_bound;
-            thi = keys[K - 1] == kEmptyKey ? __int_as_float(0x7f800000) : key_t(keys[K - 1]);
-        } else {
-            tlo = keys[K - 1] == kEmptyKeyDesc ? P.t_near : key_t(keys[K - 1]);
-            thi = t_bound;
-        }
-        bool h0, h1;
-        float e0, e1;
-        slab2(n0, n1, n2, o, inv, tlo, thi, h0, h1, e0, e1);
-        const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-        const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const bool hs = side ? h1 : h0;
-            const int rs_ = side ? r1 : r0;
-            if (hs && rs_ < 0) {
-                const int start = ~rs_, count = side ? c1 : c0;
-                for (int q = start; q < start + count; ++q) {
-                    const float4 g0 = __ldg(rec + 4 * q + 0);
-                    const float4 g1 = __ldg(rec + 4 * q + 1);
-                    const float4 g2 = __ldg(rec + 4 * q + 2);
-                    Hit h;
-                    ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-                    if (COUNT) cnt.tests++;
-                    if (h.hit) {
-                        const int64_t key = pack_key(h.t1, q);
-                        if (!DESC) {
-                            if (key > bound_key && key < keys[K - 1]) {
-                                kbuf_insert_asc<K>(keys, d2, key, h.D2);
-                                if (COUNT) cnt.inserted++;
-                            }
-                        } else {
-                            if (key < bound_key && key > keys[K - 1]) {
-                                kbuf_insert_desc<K>(keys, d2, key, h.D2);
-                                if (COUNT) cnt.inserted++;
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        const bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
-        // current pruning bounds after the leaves of this node
-        float cur_lo, cur_hi;
-        if (!DESC) {
-            cur_lo = tlo;
-            cur_hi = keys[K - 1] == kEmptyKey ? __int_as_float(0x7f800000) : key_t(keys[K - 1]);
-        } else {
-            cur_lo = keys[K - 1] == kEmptyKeyDesc ? P.t_near : key_t(keys[K - 1]);
-            cur_hi = thi;
-        }
-        (void)cur_lo;
-        if (i0 && i1) {
-            // near child first (ascending) / far child first (descending)
-            const bool first0 = DESC ? (e0 >= e1) : (e0 <= e1);
-            const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
-            const float ts = first0 ? e1 : e0;
-            if (sp < kStackSize) {
-                stack[sp] = ns;
-                stack_t[sp] = ts;
-                ++sp;
-            } else {
-                atomicOr(err, kErrStack);
-            }
-            node = nf;
-        } else if (i0) {
-            node = r0;
-        } else if (i1) {
-            node = r1;
-        } else {
-            // pop, skipping boxes whose entry now lies past the ascending bound
-            bool found = false;
-            while (sp > 0) {
-                --sp;
-                if (DESC || stack_t[sp] <= cur_hi) {
-                    node = stack[sp];
-                    found = true;
-                    break;
-                }
-            }
-            if (!found) break;
-        }
-    }
-}
-
+// ---------------------------------------------------------------------------------------------
+// Forward: one streaming pass per ray.
+//
+// Near-first stack traversal; a register buffer holds up to K *pending* hits (found, not yet
+// composited) in (t1, id) order.  The stack keeps, per entry, the running minimum of the box
+// entries below it, so after each node the smallest entry t_min of every box still to visit is
+// known: a pending hit with t1 < t_min can no longer be preceded by an undiscovered hit, and is
+// composited at once (Eq. 3); the ray stops traversing as soon as T < eps1 or k_max hits are
+// composited (Sec. 3).  If the buffer overflows, the pass keeps exactness with a key cap (no
+// hit at or beyond a dropped key is accepted or composited) and a new pass resumes after the
+// last composited key -- so the composited sequence is always the exact sorted prefix.
+// ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
 __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
                                               const TraceParams& P, const float3 o, const float3 d, float& C0,
@@ -217,6 +124,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                                               int64_t& last_key, int& count, Counters& cnt, int* err) {
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float eps = fmaxf(P.eps1, 1e-30f);
+    const float INF = __int_as_float(0x7f800000);
     T = 1.f;
     C0 = C1 = C2 = 0.f;
     depth = 0.f;
@@ -224,12 +132,15 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
     last_key = -1;
     int64_t lo_key = -1;
     bool done = false;
-    int rounds = 0;
+    int passes = 0;
+    int st_node[kStackSize];
+    float st_e[kStackSize], st_b[kStackSize];
     while (!done) {
-        if (++rounds > P.max_rounds) {
+        if (++passes > P.max_rounds) {
             atomicOr(err, kErrLoopGuard);
             break;
         }
+        if (COUNT) cnt.rounds++;
         int64_t keys[K];
         float d2[K];
 #pragma unroll
@@ -237,35 +148,150 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
             keys[s] = kEmptyKey;
             d2[s] = 0.f;
         }
-        if (COUNT) cnt.rounds++;
-        traverse_round<K, false, COUNT>(rec, nodes, P, o, d, inv, lo_key, keys, d2, cnt, err);
+        int64_t cap = kEmptyKey;  // hits must have key < cap (tightened on overflow)
+        const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
+        int sp = 0, node = 0, visits = 0;
+        auto composite_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            const float a = response_alpha(sh.x, d2[0]);
+            const float w = __fmul_rn(T, a);
+            C0 = fmaf(w, sh.y, C0);
+            C1 = fmaf(w, sh.z, C1);
+            C2 = fmaf(w, sh.w, C2);
+            depth = fmaf(w, key_t(key), depth);
+            T = __fmul_rn(T, __fsub_rn(1.f, a));
+            ++count;
+            last_key = key;
+            if (COUNT) cnt.hits++;
+            if (T < eps || count >= P.k_max) done = true;
+            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+        };
+        while (true) {
+            if (++visits > P.max_visits) {
+                atomicOr(err, kErrLoopGuard);
+                done = true;
+                break;
+            }
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            if (COUNT) cnt.nodes++;
+            float en0, ex0, en1, ex1;
+            slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+            float e0 = fmaxf(en0, tlo), e1 = fmaxf(en1, tlo);
+            bool h0, h1;
+            {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                h0 = e0 <= fminf(ex0, tcap);
+                h1 = e1 <= fminf(ex1, tcap);
+                if (h0 && e0 > tK) { h0 = false; cap = min(cap, pack_key(e0, 0)); }
+                if (h1 && e1 > tK) { h1 = false; cap = min(cap, pack_key(e1, 0)); }
+            }
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            if (!done) {
-                const int64_t key = keys[s];
-                if (key == kEmptyKey) {
-                    done = true;
-                } else {
-                    const int j = key_j(key);
-                    const float4 sh = __ldg(rec + 4 * j + 3);
-                    const float a = response_alpha(sh.x, d2[s]);
-                    const float w = __fmul_rn(T, a);
-                    C0 = fmaf(w, sh.y, C0);
-                    C1 = fmaf(w, sh.z, C1);
-                    C2 = fmaf(w, sh.w, C2);
-                    depth = fmaf(w, key_t(key), depth);
-                    T = __fmul_rn(T, __fsub_rn(1.f, a));
-                    ++count;
-                    last_key = key;
-                    if (COUNT) cnt.hits++;
-                    if (T < eps || count >= P.k_max) done = true;
+            for (int side = 0; side < 2; ++side) {
+                const bool hs = side ? h1 : h0;
+                const int rr = side ? r1 : r0;
+                if (hs && rr < 0) {
+                    const int start = ~rr, num = side ? c1 : c0;
+                    for (int q = start; q < start + num; ++q) {
+                        const float4 g0 = __ldg(rec + 4 * q + 0);
+                        const float4 g1 = __ldg(rec + 4 * q + 1);
+                        const float4 g2 = __ldg(rec + 4 * q + 2);
+                        Hit h;
+                        ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                        if (COUNT) cnt.tests++;
+                        if (h.hit) {
+                            const int64_t key = pack_key(h.t1, q);
+                            if (key > lo_key && key < cap) {
+                                if (key < keys[K - 1]) {
+                                    if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];  // evicted
+                                    kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                    if (COUNT) cnt.inserted++;
+                                } else {
+                                    cap = key;  // rejected: buffer full of nearer hits
+                                }
+                            }
+                        }
+                    }
                 }
             }
+            bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+            {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                if (i0 && e0 > tcap) i0 = false;
+                if (i1 && e1 > tcap) i1 = false;
+                if (i0 && e0 > tK) { i0 = false; cap = min(cap, pack_key(e0, 0)); }
+                if (i1 && e1 > tK) { i1 = false; cap = min(cap, pack_key(e1, 0)); }
+            }
+            const float top = sp > 0 ? st_b[sp - 1] : INF;
+            int next = -1;
+            float bound = INF;
+            if (i0 && i1) {
+                const bool first0 = e0 <= e1;
+                const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
+                const float ef = first0 ? e0 : e1, es = first0 ? e1 : e0;
+                if (sp < kStackSize) {
+                    st_node[sp] = ns;
+                    st_e[sp] = es;
+                    st_b[sp] = fminf(es, top);
+                    ++sp;
+                } else {
+                    atomicOr(err, kErrStack);
+                }
+                next = nf;
+                bound = fminf(ef, st_b[sp - 1]);
+            } else if (i0) {
+                next = r0;
+                bound = fminf(e0, top);
+            } else if (i1) {
+                next = r1;
+                bound = fminf(e1, top);
+            } else {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                while (sp > 0) {
+                    --sp;
+                    const float e = st_e[sp];
+                    if (e > tcap) continue;
+                    if (e > tK) {
+                        cap = min(cap, pack_key(e, 0));
+                        continue;
+                    }
+                    next = st_node[sp];
+                    bound = fminf(e, sp > 0 ? st_b[sp - 1] : INF);
+                    break;
+                }
+            }
+            // composite every pending hit that no unvisited box can precede
+            while (!done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
+            if (done || next < 0) break;
+            node = next;
         }
-        if (!done) lo_key = keys[K - 1];
+        while (!done && keys[0] != kEmptyKey) composite_front();
+        if (!done) {
+            if (cap == kEmptyKey) done = true;  // every hit beyond lo_key was seen
+            else lo_key = last_key;             // overflow: resume after the last composited hit
+        }
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Adjoint: the mirror image.  Far-first traversal (by box exit), a descending buffer of pending
+// hits with key below the upper bound (initially just above the last composited key), and a
+// running maximum of the stacked box exits: a pending hit with t1 above it is the farthest
+// unprocessed hit and is replayed at once, back to front.  Boxes entering beyond the last
+// composited hit are pruned.  Overflow is handled with a key floor and a further pass.
+// ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
 __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
                                                const TraceParams& P, const float3 o, const float3 d, float T_final,
@@ -273,13 +299,17 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                                                float4* __restrict__ gtmp, Counters& cnt, int* err) {
     if (n_hits <= 0) return;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-    int64_t hi_key = last_key + 1;
+    const float NINF = __int_as_float(0xff800000);
+    constexpr int64_t kFloorJ = 0x7fffffff;
+    int64_t hi_key = last_key + 1;  // exclusive upper bound
     float Tn = T_final;
     float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
     int remaining = n_hits;
-    int rounds = 0;
+    int passes = 0;
+    int st_node[kStackSize];
+    float st_x[kStackSize], st_b[kStackSize];
     while (remaining > 0) {
-        if (++rounds > P.max_rounds) {
+        if (++passes > P.max_rounds) {
             atomicOr(err, kErrLoopGuard);
             break;
         }
@@ -291,49 +321,160 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
             keys[s] = kEmptyKeyDesc;
             d2[s] = 0.f;
         }
-        traverse_round<K, true, COUNT>(rec, nodes, P, o, d, inv, hi_key, keys, d2, cnt, err);
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            const int64_t key = keys[s];
-            if (remaining > 0 && key != kEmptyKeyDesc) {
-                const int j = key_j(key);
-                const float4 g0 = __ldg(rec + 4 * j + 0);
-                const float4 g1 = __ldg(rec + 4 * j + 1);
-                const float4 g2 = __ldg(rec + 4 * j + 2);
-                const float4 sh = __ldg(rec + 4 * j + 3);
-                Hit h;
-                ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-                const float e = expf(__fmul_rn(-0.5f, h.D2));
-                const float a = __fmul_rn(sh.x, e);
-                const float om = __fsub_rn(1.f, a);
-                const float Ti = __fdiv_rn(Tn, om);
-                const float w = Ti * a;
-                // dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A))
-                const float dLda = Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) +
-                                         gA * (1.f - UA));
-                U0 = fmaf(a, sh.y, om * U0);
-                U1 = fmaf(a, sh.z, om * U1);
-                U2 = fmaf(a, sh.w, om * U2);
-                UA = fmaf(om, UA, a);
-                Tn = Ti;
-                const float gD2 = -0.5f * a * dLda;
-                const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-                // dL/dm = -M^T (2 gD2 p)
-                const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
-                const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
-                const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
-                float4* gp = gtmp + 4 * j;
-                atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
-                atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
-                atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
-                atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
-                --remaining;
-                hi_key = key;
-                if (COUNT) cnt.hits++;
+        int64_t floor_key = -1;  // hits must have key > floor_key (raised on overflow)
+        const float thi = key_t(hi_key);
+        int sp = 0, node = 0, visits = 0;
+        bool stop = false;
+        auto replay_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 g0 = __ldg(rec + 4 * j + 0);
+            const float4 g1 = __ldg(rec + 4 * j + 1);
+            const float4 g2 = __ldg(rec + 4 * j + 2);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            Hit h;
+            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+            const float e = expf(__fmul_rn(-0.5f, h.D2));
+            const float a = __fmul_rn(sh.x, e);
+            const float om = __fsub_rn(1.f, a);
+            const float Ti = __fdiv_rn(Tn, om);
+            const float w = Ti * a;
+            // dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A))
+            const float dLda =
+                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
+            U0 = fmaf(a, sh.y, om * U0);
+            U1 = fmaf(a, sh.z, om * U1);
+            U2 = fmaf(a, sh.w, om * U2);
+            UA = fmaf(om, UA, a);
+            Tn = Ti;
+            const float gD2 = -0.5f * a * dLda;
+            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+            // dL/dm = -M^T (2 gD2 p)
+            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
+            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            float4* gp = gtmp + 4 * j;
+            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
+            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
+            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
+            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+            --remaining;
+            hi_key = key;
+            if (COUNT) cnt.hits++;
+            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+        };
+        while (true) {
+            if (++visits > P.max_visits) {
+                atomicOr(err, kErrLoopGuard);
+                stop = true;
+                break;
             }
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            if (COUNT) cnt.nodes++;
+            float en0, ex0, en1, ex1;
+            slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+            bool h0, h1;
+            {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                h0 = en0 <= thi && ex0 >= tfl && ex0 >= en0;
+                h1 = en1 <= thi && ex1 >= tfl && ex1 >= en1;
+                if (h0 && ex0 < tK) { h0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                if (h1 && ex1 < tK) { h1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const bool hs = side ? h1 : h0;
+                const int rr = side ? r1 : r0;
+                if (hs && rr < 0) {
+                    const int start = ~rr, num = side ? c1 : c0;
+                    for (int q = start; q < start + num; ++q) {
+                        const float4 g0 = __ldg(rec + 4 * q + 0);
+                        const float4 g1 = __ldg(rec + 4 * q + 1);
+                        const float4 g2 = __ldg(rec + 4 * q + 2);
+                        Hit h;
+                        ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                        if (COUNT) cnt.tests++;
+                        if (h.hit) {
+                            const int64_t key = pack_key(h.t1, q);
+                            if (key < hi_key && key > floor_key) {
+                                if (key > keys[K - 1]) {
+                                    if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];  // evicted
+                                    kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                    if (COUNT) cnt.inserted++;
+                                } else {
+                                    floor_key = key;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+            {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                if (i0 && ex0 < tfl) i0 = false;
+                if (i1 && ex1 < tfl) i1 = false;
+                if (i0 && ex0 < tK) { i0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                if (i1 && ex1 < tK) { i1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+            }
+            const float top = sp > 0 ? st_b[sp - 1] : NINF;
+            int next = -1;
+            float bound = NINF;
+            if (i0 && i1) {
+                const bool first0 = ex0 >= ex1;
+                const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
+                const float xf = first0 ? ex0 : ex1, xs = first0 ? ex1 : ex0;
+                if (sp < kStackSize) {
+                    st_node[sp] = ns;
+                    st_x[sp] = xs;
+                    st_b[sp] = fmaxf(xs, top);
+                    ++sp;
+                } else {
+                    atomicOr(err, kErrStack);
+                }
+                next = nf;
+                bound = fmaxf(xf, st_b[sp - 1]);
+            } else if (i0) {
+                next = r0;
+                bound = fmaxf(ex0, top);
+            } else if (i1) {
+                next = r1;
+                bound = fmaxf(ex1, top);
+            } else {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                while (sp > 0) {
+                    --sp;
+                    const float x = st_x[sp];
+                    if (x < tfl) continue;
+                    if (x < tK) {
+                        floor_key = max(floor_key, pack_key(x, kFloorJ));
+                        continue;
+                    }
+                    next = st_node[sp];
+                    bound = fmaxf(x, sp > 0 ? st_b[sp - 1] : NINF);
+                    break;
+                }
+            }
+            // replay every pending hit that no unvisited box can follow
+            while (remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound) replay_front();
+            if (remaining == 0 || next < 0) break;
+            node = next;
         }
-        if (remaining > 0 && keys[K - 1] == kEmptyKeyDesc) {
-            atomicOr(err, kErrReplayMismatch);
+        if (stop) break;
+        while (remaining > 0 && keys[0] != kEmptyKeyDesc) replay_front();
+        if (remaining > 0 && floor_key < 0) {
+            atomicOr(err, kErrReplayMismatch);  // the forward saw hits that this pass did not
             break;
         }
     }

@@ -1,0 +1,91 @@
+"""Autotuner front end: candidate tunables, a JSON cache, and the native rs_tune sweep.
+
+The sweep itself (rebuild + render + adjoint per candidate, CUDA-event timed) runs in
+libraysplats.so (`rs_tune`); this module picks the candidates and caches the winner keyed by
+(GPU name, Gaussian-count bucket, ray-count bucket, camera count, backward or not).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import json
+import math
+import os
+
+import torch
+
+from . import native
+
+CACHE_ENV = "RAYSPLATS_TUNE_CACHE"
+
+
+def default_cache_path() -> str:
+    return os.environ.get(CACHE_ENV, os.path.join(os.path.expanduser("~"), ".cache", "raysplats_tune.json"))
+
+
+def candidates(tiles=((8, 4), (4, 8), (16, 2)), kbufs=(8, 16, 32), leaves=(2, 4, 8), warps=(2, 4),
+               persistent=1, morton_bits=21):
+    out = []
+    for (tw, th), k, leaf, w in itertools.product(tiles, kbufs, leaves, warps):
+        t = native.RsTuneParams(tw, th, k, leaf, morton_bits, persistent, w)
+        out.append(t)
+    return out
+
+
+def cache_key(n_gauss, n_rays, n_cams, backward, device=None) -> str:
+    name = torch.cuda.get_device_name(device) if torch.cuda.is_available() else "cpu"
+    b = lambda x: 2 ** int(round(math.log2(max(1, x))))  # noqa: E731
+    return f"{name}|n{b(n_gauss)}|r{b(n_rays)}|c{n_cams}|{'fb' if backward else 'f'}"
+
+
+def autotune(params5, cams, render_params, d_rgb=None, d_alpha=None, cands=None, reps=3, cache=True,
+             cache_path=None, stream=None):
+    """Run the sweep (or read the cache).  params5 = (means, quats, scales, opacities, rgb) CUDA
+    tensors; cams: workloads.Cameras; render_params: renderer.RenderParams.  Returns
+    (best RsTuneParams, {candidate dict as json: ms})."""
+    lib = native.load()
+    n = params5[0].shape[0]
+    cam_arr = native.cameras_to_ctypes(cams)
+    P = int(sum(c.width * c.height for c in cam_arr))
+    key = cache_key(n, P, len(cam_arr), d_rgb is not None)
+    path = cache_path or default_cache_path()
+    if cache and os.path.exists(path):
+        try:
+            db = json.load(open(path))
+            if key in db:
+                return native.RsTuneParams(**db[key]["best"]), db[key].get("ms", {})
+        except Exception:
+            pass
+    cands = cands or candidates()
+    arr = (native.RsTuneParams * len(cands))(*cands)
+    dev = params5[0].device
+    out = (torch.empty((P, 3), device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
+    frame = native.RsFrame(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+    g = native.RsGaussians(n, *[t.data_ptr() for t in params5])
+    grads = None
+    dl = None
+    if d_rgb is not None:
+        scratch = [torch.zeros((n, w), device=dev) for w in (3, 4, 3, 1, 3)]
+        grads = native.RsGaussianGrads(*[t.data_ptr() for t in scratch])
+        dl = native.RsFrameGrad(d_rgb.data_ptr(), None if d_alpha is None else d_alpha.data_ptr())
+    best = native.RsTuneParams()
+    ms = (ctypes.c_float * len(cands))()
+    rp = render_params.to_c()
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    native.check(lib.rs_tune(ctypes.byref(g), float(render_params.Q), cam_arr, len(cam_arr), ctypes.byref(rp), arr,
+                             len(cands), int(reps), ctypes.byref(frame), None if dl is None else ctypes.byref(dl),
+                             None if grads is None else ctypes.byref(grads), ctypes.byref(best), ms, s))
+    table = {json.dumps(c.as_dict(), sort_keys=True): float(m) for c, m in zip(cands, ms)}
+    if cache:
+        db = {}
+        if os.path.exists(path):
+            try:
+                db = json.load(open(path))
+            except Exception:
+                db = {}
+        db[key] = {"best": best.as_dict(), "ms": table}
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(db, f, indent=1)
+        os.replace(path + ".tmp", path)
+    return best, table

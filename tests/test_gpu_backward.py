@@ -101,9 +101,11 @@ def test_autograd_function_matches_direct_backward():
     r.render(cams, prm)
     ref = r.backward(w.contiguous(), wa.contiguous())
     torch.cuda.synchronize()
+    # float atomics accumulate in a different order on each call: compare in relative L2
     for leaf, k in zip(leaves, KEYS):
-        np.testing.assert_allclose(leaf.grad.cpu().numpy().reshape(-1), ref[k].cpu().numpy().reshape(-1),
-                                   rtol=1e-5, atol=1e-6)
+        a = leaf.grad.cpu().numpy().astype(np.float64).reshape(-1)
+        b = ref[k].cpu().numpy().astype(np.float64).reshape(-1)
+        assert rel_l2(a, b) < 1e-5, (k, rel_l2(a, b))
     r.close()
 
 
