@@ -130,7 +130,11 @@ typedef struct {
  *                   of the largest scale) below the top four levels
  *   persistent      0: one launch per camera; 1: one persistent launch over all cameras'
  *                   ray tiles through a device work queue
- *   block_warps     warps per CTA: 1..16 */
+ *   block_warps     warps per CTA: 1..4
+ *   traversal       0: each lane traverses its own ray (depth first); 1: the 32 rays of a
+ *                   tile traverse as a warp packet (shared node sequence, per-ray state, depth
+ *                   first); 2: warp packet in best-first order of box entry (a priority queue
+ *                   distributed over the warp's registers) */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t kbuf;
@@ -138,6 +142,7 @@ typedef struct {
     int32_t morton_bits;
     int32_t persistent;
     int32_t block_warps;
+    int32_t traversal;
 } rs_tune_params;
 
 typedef struct rs_accel rs_accel;
@@ -161,7 +166,7 @@ int32_t rs_abi_version(void);
 const char* rs_last_error(void);
 
 /* Fill *out with the default tunables (8x4 tiles, kbuf 16, leaf 4, 63-bit codes,
- * persistent launch, 4 warps per CTA). */
+ * persistent launch, 4 warps per CTA, warp-packet traversal). */
 rs_status rs_default_tune(rs_tune_params* out);
 
 /* Build the acceleration structure of a scene (LBVH): per-Gaussian render records

@@ -64,6 +64,9 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
         return set_error(RS_ERR_INVALID_ARG, "morton_bits %d: must be 10, 20 (extended) or 21", t->morton_bits);
     if (t->block_warps < 1 || t->block_warps > 4)
         return set_error(RS_ERR_INVALID_ARG, "block_warps %d: must be 1..4", t->block_warps);
+    if (t->traversal < 0 || t->traversal > 2)
+        return set_error(RS_ERR_INVALID_ARG, "traversal %d: must be 0 (per ray), 1 (warp packet) or 2 (best-first "
+                         "warp packet)", t->traversal);
     return RS_OK;
 }
 
@@ -97,6 +100,7 @@ rs_status rs_default_tune(rs_tune_params* out) {
     out->morton_bits = 21;
     out->persistent = 1;
     out->block_warps = 4;
+    out->traversal = 1;
     return RS_OK;
 }
 
@@ -281,16 +285,18 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         A.cam_single = -1;
         A.total_tiles = tiles;
         if (cudaMemsetAsync(S->queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return cuda_check("queue reset");
-        const int grid = (int)std::min<int64_t>(persistent_grid(false, tune->kbuf, block, count, sm_count()),
-                                                (tiles + tune->block_warps - 1) / tune->block_warps);
-        const cudaError_t e = launch_forward(A, tune->kbuf, true, count, std::max(grid, 1), block, s);
+        const int grid = (int)std::min<int64_t>(
+            persistent_grid(false, tune->kbuf, block, count, tune->traversal, sm_count()),
+            (tiles + tune->block_warps - 1) / tune->block_warps);
+        const cudaError_t e = launch_forward(A, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
+                                             block, s);
         if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
     } else {
         for (int c = 0; c < n_cams; ++c) {
             A.cam_single = c;
             A.total_tiles = (int64_t)table[(size_t)c].tiles_x * table[(size_t)c].tiles_y;
             const int grid = (int)((A.total_tiles + tune->block_warps - 1) / tune->block_warps);
-            const cudaError_t e = launch_forward(A, tune->kbuf, false, count, grid, block, s);
+            const cudaError_t e = launch_forward(A, tune->kbuf, false, count, tune->traversal, grid, block, s);
             if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
         }
     }
@@ -356,9 +362,11 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         A.total_tiles = S->total_tiles;
         if (cudaMemsetAsync(S->queue + 1, 0, sizeof(unsigned long long), s) != cudaSuccess)
             return cuda_check("queue reset");
-        const int grid = (int)std::min<int64_t>(persistent_grid(true, tune->kbuf, block, count, sm_count()),
-                                                (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
-        const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, std::max(grid, 1), block, s);
+        const int grid = (int)std::min<int64_t>(
+            persistent_grid(true, tune->kbuf, block, count, tune->traversal, sm_count()),
+            (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
+        const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
+                                              block, s);
         if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
     } else {
         for (int c = 0; c < S->n_cams; ++c) {
@@ -366,7 +374,8 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
             A.cam_single = c;
             A.total_tiles = (int64_t)D.tiles_x * D.tiles_y;
             const int grid = (int)((A.total_tiles + tune->block_warps - 1) / tune->block_warps);
-            const cudaError_t e = launch_backward(A, B, tune->kbuf, false, count, grid, block, s);
+            const cudaError_t e =
+                launch_backward(A, B, tune->kbuf, false, count, tune->traversal, grid, block, s);
             if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
         }
     }

@@ -481,6 +481,844 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
 }
 
 // ---------------------------------------------------------------------------------------------
+// Warp-packet variants.  The 32 lanes of a warp (one ray tile) traverse together: the node
+// sequence is shared (uniform loads are broadcast, descent is decided by warp votes: a child
+// is visited when any active lane needs it), while each lane keeps its own streaming state --
+// pending buffer, key cap, and per-lane stack entries (a lane that does not need a stacked box
+// records +inf, so its finalisation bound is unaffected).  The result of every lane is exactly
+// that of the per-ray traversal: a lane only tests the boxes and Gaussians it would have
+// tested, in an order that does not change what it composites.
+// ---------------------------------------------------------------------------------------------
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                                     const TraceParams& P, bool valid, const float3 o,
+                                                     const float3 d, float& C0, float& C1, float& C2, float& T,
+                                                     float& depth, int64_t& last_key, int& count, Counters& cnt,
+                                                     int* err) {
+    const unsigned FULL = 0xffffffffu;
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float eps = fmaxf(P.eps1, 1e-30f);
+    const float INF = __int_as_float(0x7f800000);
+    T = 1.f;
+    C0 = C1 = C2 = 0.f;
+    depth = 0.f;
+    count = 0;
+    last_key = -1;
+    int64_t lo_key = -1;
+    bool done = !valid;
+    int passes = 0;
+    int st_node[kStackSize];
+    float st_e[kStackSize], st_b[kStackSize];
+    while (__any_sync(FULL, !done)) {
+        if (++passes > P.max_rounds) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        if (COUNT && !done) cnt.rounds++;
+        bool active = !done;
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKey;
+            d2[s] = 0.f;
+        }
+        int64_t cap = kEmptyKey;
+        const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
+        int sp = 0, node = 0, visits = 0;
+        auto composite_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            const float a = response_alpha(sh.x, d2[0]);
+            const float w = __fmul_rn(T, a);
+            C0 = fmaf(w, sh.y, C0);
+            C1 = fmaf(w, sh.z, C1);
+            C2 = fmaf(w, sh.w, C2);
+            depth = fmaf(w, key_t(key), depth);
+            T = __fmul_rn(T, __fsub_rn(1.f, a));
+            ++count;
+            last_key = key;
+            if (COUNT) cnt.hits++;
+            if (T < eps || count >= P.k_max) done = true;
+            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+        };
+        while (true) {
+            if (++visits > P.max_visits) {
+                if ((threadIdx.x & 31) == 0) atomicOr(err, kErrLoopGuard);
+                done = true;
+                break;
+            }
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            if (COUNT && active) cnt.nodes++;
+            float en0, ex0, en1, ex1;
+            slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+            const float e0 = fmaxf(en0, tlo), e1 = fmaxf(en1, tlo);
+            bool h0 = false, h1 = false;
+            if (active) {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                h0 = e0 <= fminf(ex0, tcap);
+                h1 = e1 <= fminf(ex1, tcap);
+                if (h0 && e0 > tK) { h0 = false; cap = min(cap, pack_key(e0, 0)); }
+                if (h1 && e1 > tK) { h1 = false; cap = min(cap, pack_key(e1, 0)); }
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int rr = side ? r1 : r0;
+                const bool want = (side ? h1 : h0) && rr < 0;
+                if (__any_sync(FULL, want)) {
+                    const int start = ~rr, num = side ? c1 : c0;
+                    for (int q = start; q < start + num; ++q) {
+                        if (want) {
+                            const float4 g0 = __ldg(rec + 4 * q + 0);
+                            const float4 g1 = __ldg(rec + 4 * q + 1);
+                            const float4 g2 = __ldg(rec + 4 * q + 2);
+                            Hit h;
+                            ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                            if (COUNT) cnt.tests++;
+                            if (h.hit) {
+                                const int64_t key = pack_key(h.t1, q);
+                                if (key > lo_key && key < cap) {
+                                    if (key < keys[K - 1]) {
+                                        if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
+                                        kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                        if (COUNT) cnt.inserted++;
+                                    } else {
+                                        cap = key;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+            if (active) {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                if (i0 && e0 > tcap) i0 = false;
+                if (i1 && e1 > tcap) i1 = false;
+                if (i0 && e0 > tK) { i0 = false; cap = min(cap, pack_key(e0, 0)); }
+                if (i1 && e1 > tK) { i1 = false; cap = min(cap, pack_key(e1, 0)); }
+            }
+            const bool any0 = __any_sync(FULL, i0), any1 = __any_sync(FULL, i1);
+            const float top = sp > 0 ? st_b[sp - 1] : INF;
+            int next = -1;
+            float bound = INF;
+            if (any0 && any1) {
+                const int v0 = __popc(__ballot_sync(FULL, i0 && (!i1 || e0 <= e1)));
+                const int v1 = __popc(__ballot_sync(FULL, i1 && (!i0 || e1 < e0)));
+                const bool first0 = v0 >= v1;
+                const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
+                const bool need_f = first0 ? i0 : i1, need_s = first0 ? i1 : i0;
+                const float ef = first0 ? e0 : e1, es = first0 ? e1 : e0;
+                if (sp < kStackSize) {
+                    st_node[sp] = ns;
+                    st_e[sp] = need_s ? es : INF;
+                    st_b[sp] = fminf(st_e[sp], top);
+                    ++sp;
+                } else if ((threadIdx.x & 31) == 0) {
+                    atomicOr(err, kErrStack);
+                }
+                next = nf;
+                bound = fminf(need_f ? ef : INF, sp > 0 ? st_b[sp - 1] : INF);
+            } else if (any0) {
+                next = r0;
+                bound = fminf(i0 ? e0 : INF, top);
+            } else if (any1) {
+                next = r1;
+                bound = fminf(i1 ? e1 : INF, top);
+            } else {
+                while (sp > 0) {
+                    --sp;
+                    const float e = st_e[sp];
+                    bool need = false;
+                    if (active && e != INF) {
+                        const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                        const bool full = keys[K - 1] != kEmptyKey;
+                        const float tK = full ? key_t(keys[K - 1]) : INF;
+                        if (e <= tcap) {
+                            if (e > tK) cap = min(cap, pack_key(e, 0));
+                            else need = true;
+                        }
+                    }
+                    if (__any_sync(FULL, need)) {
+                        next = st_node[sp];
+                        bound = fminf(need ? e : INF, sp > 0 ? st_b[sp - 1] : INF);
+                        break;
+                    }
+                }
+            }
+            while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
+            active = active && !done;
+            if (next < 0 || !__any_sync(FULL, active)) break;
+            node = next;
+        }
+        while (active && !done && keys[0] != kEmptyKey) composite_front();
+        if (active && !done) {
+            if (cap == kEmptyKey) done = true;
+            else lo_key = last_key;
+        }
+    }
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_backward_packet(const float4* __restrict__ rec,
+                                                      const float4* __restrict__ nodes, const TraceParams& P,
+                                                      const float3 o, const float3 d, float T_final,
+                                                      int64_t last_key, int n_hits, const float gC[3], float gA,
+                                                      float4* __restrict__ gtmp, Counters& cnt, int* err) {
+    const unsigned FULL = 0xffffffffu;
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float NINF = __int_as_float(0xff800000);
+    constexpr int64_t kFloorJ = 0x7fffffff;
+    int64_t hi_key = last_key + 1;
+    float Tn = T_final;
+    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    int remaining = n_hits > 0 ? n_hits : 0;
+    int passes = 0;
+    int st_node[kStackSize];
+    float st_x[kStackSize], st_b[kStackSize];
+    while (__any_sync(FULL, remaining > 0)) {
+        if (++passes > P.max_rounds) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        if (COUNT && remaining > 0) cnt.rounds++;
+        bool active = remaining > 0;
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKeyDesc;
+            d2[s] = 0.f;
+        }
+        int64_t floor_key = -1;
+        const float thi = key_t(hi_key);
+        int sp = 0, node = 0, visits = 0;
+        bool stop = false;
+        auto replay_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 g0 = __ldg(rec + 4 * j + 0);
+            const float4 g1 = __ldg(rec + 4 * j + 1);
+            const float4 g2 = __ldg(rec + 4 * j + 2);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            Hit h;
+            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+            const float e = expf(__fmul_rn(-0.5f, h.D2));
+            const float a = __fmul_rn(sh.x, e);
+            const float om = __fsub_rn(1.f, a);
+            const float Ti = __fdiv_rn(Tn, om);
+            const float w = Ti * a;
+            const float dLda =
+                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
+            U0 = fmaf(a, sh.y, om * U0);
+            U1 = fmaf(a, sh.z, om * U1);
+            U2 = fmaf(a, sh.w, om * U2);
+            UA = fmaf(om, UA, a);
+            Tn = Ti;
+            const float gD2 = -0.5f * a * dLda;
+            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
+            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            float4* gp = gtmp + 4 * j;
+            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
+            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
+            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
+            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+            --remaining;
+            hi_key = key;
+            if (COUNT) cnt.hits++;
+            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+        };
+        while (true) {
+            if (++visits > P.max_visits) {
+                if ((threadIdx.x & 31) == 0) atomicOr(err, kErrLoopGuard);
+                stop = true;
+                break;
+            }
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            if (COUNT && active) cnt.nodes++;
+            float en0, ex0, en1, ex1;
+            slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+            bool h0 = false, h1 = false;
+            if (active) {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                h0 = en0 <= thi && ex0 >= tfl && ex0 >= en0;
+                h1 = en1 <= thi && ex1 >= tfl && ex1 >= en1;
+                if (h0 && ex0 < tK) { h0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                if (h1 && ex1 < tK) { h1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+            }
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                const int rr = side ? r1 : r0;
+                const bool want = (side ? h1 : h0) && rr < 0;
+                if (__any_sync(FULL, want)) {
+                    const int start = ~rr, num = side ? c1 : c0;
+                    for (int q = start; q < start + num; ++q) {
+                        if (want) {
+                            const float4 g0 = __ldg(rec + 4 * q + 0);
+                            const float4 g1 = __ldg(rec + 4 * q + 1);
+                            const float4 g2 = __ldg(rec + 4 * q + 2);
+                            Hit h;
+                            ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                            if (COUNT) cnt.tests++;
+                            if (h.hit) {
+                                const int64_t key = pack_key(h.t1, q);
+                                if (key < hi_key && key > floor_key) {
+                                    if (key > keys[K - 1]) {
+                                        if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
+                                        kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                        if (COUNT) cnt.inserted++;
+                                    } else {
+                                        floor_key = key;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+            if (active) {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                if (i0 && ex0 < tfl) i0 = false;
+                if (i1 && ex1 < tfl) i1 = false;
+                if (i0 && ex0 < tK) { i0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                if (i1 && ex1 < tK) { i1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+            }
+            const bool any0 = __any_sync(FULL, i0), any1 = __any_sync(FULL, i1);
+            const float top = sp > 0 ? st_b[sp - 1] : NINF;
+            int next = -1;
+            float bound = NINF;
+            if (any0 && any1) {
+                const int v0 = __popc(__ballot_sync(FULL, i0 && (!i1 || ex0 >= ex1)));
+                const int v1 = __popc(__ballot_sync(FULL, i1 && (!i0 || ex1 > ex0)));
+                const bool first0 = v0 >= v1;
+                const int nf = first0 ? r0 : r1, ns = first0 ? r1 : r0;
+                const bool need_f = first0 ? i0 : i1, need_s = first0 ? i1 : i0;
+                const float xf = first0 ? ex0 : ex1, xs = first0 ? ex1 : ex0;
+                if (sp < kStackSize) {
+                    st_node[sp] = ns;
+                    st_x[sp] = need_s ? xs : NINF;
+                    st_b[sp] = fmaxf(st_x[sp], top);
+                    ++sp;
+                } else if ((threadIdx.x & 31) == 0) {
+                    atomicOr(err, kErrStack);
+                }
+                next = nf;
+                bound = fmaxf(need_f ? xf : NINF, sp > 0 ? st_b[sp - 1] : NINF);
+            } else if (any0) {
+                next = r0;
+                bound = fmaxf(i0 ? ex0 : NINF, top);
+            } else if (any1) {
+                next = r1;
+                bound = fmaxf(i1 ? ex1 : NINF, top);
+            } else {
+                while (sp > 0) {
+                    --sp;
+                    const float x = st_x[sp];
+                    bool need = false;
+                    if (active && x != NINF) {
+                        const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                        const bool full = keys[K - 1] != kEmptyKeyDesc;
+                        const float tK = full ? key_t(keys[K - 1]) : NINF;
+                        if (x >= tfl) {
+                            if (x < tK) floor_key = max(floor_key, pack_key(x, kFloorJ));
+                            else need = true;
+                        }
+                    }
+                    if (__any_sync(FULL, need)) {
+                        next = st_node[sp];
+                        bound = fmaxf(need ? x : NINF, sp > 0 ? st_b[sp - 1] : NINF);
+                        break;
+                    }
+                }
+            }
+            while (active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound) replay_front();
+            active = active && remaining > 0;
+            if (next < 0 || !__any_sync(FULL, active)) break;
+            node = next;
+        }
+        if (__any_sync(FULL, stop)) break;
+        while (active && remaining > 0 && keys[0] != kEmptyKeyDesc) replay_front();
+        if (active && remaining > 0 && floor_key < 0) {
+            atomicOr(err, kErrReplayMismatch);
+            remaining = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Best-first warp packets.  The warp keeps its unvisited nodes in a priority queue distributed
+// over the lanes' registers (kQSlots per lane, 32 * kQSlots entries); a node's priority is the
+// smallest box entry (forward) or the largest box exit (adjoint) among the lanes that need it.
+// Nodes are expanded in priority order, so the queue's extreme priority is a bound valid for
+// every lane: forward, no undiscovered hit of any lane precedes it, and pending hits nearer
+// than it are composited at once; the adjoint mirrors this back to front.  Hits therefore
+// leave the pending buffer almost as soon as they are found and one pass usually suffices.
+// A full queue drops the new node and caps (floors) the keys of every active lane, which
+// keeps the result exact at the cost of a further pass.
+// ---------------------------------------------------------------------------------------------
+constexpr int kQSlots = 4;
+
+struct WarpQueue {
+    float pr[kQSlots];  // priority (+inf = empty for the min-queue, -inf for the max-queue)
+    int nd[kQSlots];
+};
+
+template <bool MAXQ>
+__device__ __forceinline__ void wq_init(WarpQueue& q) {
+#pragma unroll
+    for (int s = 0; s < kQSlots; ++s) {
+        q.pr[s] = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+        q.nd[s] = 0;
+    }
+}
+
+// push a (uniform) entry; false when the queue is full
+template <bool MAXQ>
+__device__ __forceinline__ bool wq_push(WarpQueue& q, float pr, int node, int lane) {
+    const float empty = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+#pragma unroll
+    for (int s = 0; s < kQSlots; ++s) {
+        const unsigned m = __ballot_sync(0xffffffffu, q.pr[s] == empty);
+        if (m) {
+            if (lane == __ffs(m) - 1) {
+                q.pr[s] = pr;
+                q.nd[s] = node;
+            }
+            return true;
+        }
+    }
+    return false;
+}
+
+// extreme priority over the whole queue (uniform); empty value when the queue is empty
+template <bool MAXQ>
+__device__ __forceinline__ float wq_top(const WarpQueue& q) {
+    float v = q.pr[0];
+#pragma unroll
+    for (int s = 1; s < kQSlots; ++s) v = MAXQ ? fmaxf(v, q.pr[s]) : fminf(v, q.pr[s]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = MAXQ ? fmaxf(v, o) : fminf(v, o);
+    }
+    return v;
+}
+
+// pop the extreme entry (ties: lowest slot id); returns false when empty
+template <bool MAXQ>
+__device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int lane) {
+    const float empty = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    float v = q.pr[0];
+    int bs = 0;
+#pragma unroll
+    for (int s = 1; s < kQSlots; ++s) {
+        const bool better = MAXQ ? (q.pr[s] > v) : (q.pr[s] < v);
+        if (better) {
+            v = q.pr[s];
+            bs = s;
+        }
+    }
+    int id = lane * kQSlots + bs;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int oid = __shfl_xor_sync(0xffffffffu, id, off);
+        const bool better = MAXQ ? (ov > v || (ov == v && oid < id)) : (ov < v || (ov == v && oid < id));
+        if (better) {
+            v = ov;
+            id = oid;
+        }
+    }
+    if (v == empty) return false;
+    const int owner = id / kQSlots, slot = id % kQSlots;
+    int mine = q.nd[0];
+#pragma unroll
+    for (int s = 1; s < kQSlots; ++s)
+        if (slot == s) mine = q.nd[s];
+    node = __shfl_sync(0xffffffffu, mine, owner);
+    pr = v;
+    if (lane == owner) {
+#pragma unroll
+        for (int s = 0; s < kQSlots; ++s)
+            if (slot == s) q.pr[s] = empty;
+    }
+    return true;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                                 const TraceParams& P, bool valid, const float3 o, const float3 d,
+                                                 float& C0, float& C1, float& C2, float& T, float& depth,
+                                                 int64_t& last_key, int& count, Counters& cnt, int* err) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float eps = fmaxf(P.eps1, 1e-30f);
+    const float INF = __int_as_float(0x7f800000);
+    T = 1.f;
+    C0 = C1 = C2 = 0.f;
+    depth = 0.f;
+    count = 0;
+    last_key = -1;
+    int64_t lo_key = -1;
+    bool done = !valid;
+    int passes = 0;
+    while (__any_sync(FULL, !done)) {
+        if (++passes > P.max_rounds) {
+            if (lane == 0) atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        if (COUNT && !done) cnt.rounds++;
+        bool active = !done;
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKey;
+            d2[s] = 0.f;
+        }
+        int64_t cap = kEmptyKey;
+        const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
+        auto composite_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            const float a = response_alpha(sh.x, d2[0]);
+            const float w = __fmul_rn(T, a);
+            C0 = fmaf(w, sh.y, C0);
+            C1 = fmaf(w, sh.z, C1);
+            C2 = fmaf(w, sh.w, C2);
+            depth = fmaf(w, key_t(key), depth);
+            T = __fmul_rn(T, __fsub_rn(1.f, a));
+            ++count;
+            last_key = key;
+            if (COUNT) cnt.hits++;
+            if (T < eps || count >= P.k_max) done = true;
+            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+        };
+        auto drop_cap = [&](float e) {  // a node with packet entry e was dropped for this pass
+            if (active) cap = min(cap, pack_key(fmaxf(e, 0.f), 0));
+        };
+        WarpQueue q;
+        wq_init<false>(q);
+        wq_push<false>(q, -INF, 0, lane);
+        int visits = 0;
+        while (true) {
+            float e_node;
+            int node;
+            if (!wq_pop<false>(q, e_node, node, lane)) break;
+            // a lane needs the node unless its (conservative) entry lies past its bounds
+            bool need = false;
+            if (active) {
+                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const bool full = keys[K - 1] != kEmptyKey;
+                const float tK = full ? key_t(keys[K - 1]) : INF;
+                if (e_node <= tcap) {
+                    if (e_node > tK) cap = min(cap, pack_key(fmaxf(e_node, 0.f), 0));
+                    else need = true;
+                }
+            }
+            if (__any_sync(FULL, need)) {
+                if (++visits > P.max_visits) {
+                    if (lane == 0) atomicOr(err, kErrLoopGuard);
+                    done = true;
+                    break;
+                }
+                const float4 n0 = __ldg(nodes + 4 * node + 0);
+                const float4 n1 = __ldg(nodes + 4 * node + 1);
+                const float4 n2 = __ldg(nodes + 4 * node + 2);
+                const float4 n3 = __ldg(nodes + 4 * node + 3);
+                if (COUNT && need) cnt.nodes++;
+                float en0, ex0, en1, ex1;
+                slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+                const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+                const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+                const float e0 = fmaxf(en0, tlo), e1 = fmaxf(en1, tlo);
+                bool h0 = false, h1 = false;
+                if (need) {
+                    const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                    const bool full = keys[K - 1] != kEmptyKey;
+                    const float tK = full ? key_t(keys[K - 1]) : INF;
+                    h0 = e0 <= fminf(ex0, tcap);
+                    h1 = e1 <= fminf(ex1, tcap);
+                    if (h0 && e0 > tK) { h0 = false; cap = min(cap, pack_key(e0, 0)); }
+                    if (h1 && e1 > tK) { h1 = false; cap = min(cap, pack_key(e1, 0)); }
+                }
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int rr = side ? r1 : r0;
+                    const bool want = (side ? h1 : h0) && rr < 0;
+                    if (__any_sync(FULL, want)) {
+                        const int start = ~rr, num = side ? c1 : c0;
+                        for (int qq = start; qq < start + num; ++qq) {
+                            if (want) {
+                                const float4 g0 = __ldg(rec + 4 * qq + 0);
+                                const float4 g1 = __ldg(rec + 4 * qq + 1);
+                                const float4 g2 = __ldg(rec + 4 * qq + 2);
+                                Hit h;
+                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                                if (COUNT) cnt.tests++;
+                                if (h.hit) {
+                                    const int64_t key = pack_key(h.t1, qq);
+                                    if (key > lo_key && key < cap) {
+                                        if (key < keys[K - 1]) {
+                                            if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
+                                            kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                            if (COUNT) cnt.inserted++;
+                                        } else {
+                                            cap = key;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+                if (need) {
+                    const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                    const bool full = keys[K - 1] != kEmptyKey;
+                    const float tK = full ? key_t(keys[K - 1]) : INF;
+                    if (i0 && e0 > tcap) i0 = false;
+                    if (i1 && e1 > tcap) i1 = false;
+                    if (i0 && e0 > tK) { i0 = false; cap = min(cap, pack_key(e0, 0)); }
+                    if (i1 && e1 > tK) { i1 = false; cap = min(cap, pack_key(e1, 0)); }
+                }
+                if (__any_sync(FULL, i0)) {
+                    const float ep = warp_min(i0 ? e0 : INF);
+                    if (!wq_push<false>(q, ep, r0, lane)) drop_cap(ep);
+                }
+                if (__any_sync(FULL, i1)) {
+                    const float ep = warp_min(i1 ? e1 : INF);
+                    if (!wq_push<false>(q, ep, r1, lane)) drop_cap(ep);
+                }
+            }
+            const float bound = wq_top<false>(q);
+            while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
+            active = active && !done;
+            if (!__any_sync(FULL, active)) break;
+        }
+        while (active && !done && keys[0] != kEmptyKey) composite_front();
+        if (active && !done) {
+            if (cap == kEmptyKey) done = true;
+            else lo_key = last_key;
+        }
+    }
+}
+
+template <int K, bool COUNT>
+__device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+                                                  const TraceParams& P, const float3 o, const float3 d,
+                                                  float T_final, int64_t last_key, int n_hits, const float gC[3],
+                                                  float gA, float4* __restrict__ gtmp, Counters& cnt, int* err) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float NINF = __int_as_float(0xff800000);
+    const float INF = __int_as_float(0x7f800000);
+    constexpr int64_t kFloorJ = 0x7fffffff;
+    int64_t hi_key = last_key + 1;
+    float Tn = T_final;
+    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    int remaining = n_hits > 0 ? n_hits : 0;
+    int passes = 0;
+    while (__any_sync(FULL, remaining > 0)) {
+        if (++passes > P.max_rounds) {
+            if (lane == 0) atomicOr(err, kErrLoopGuard);
+            break;
+        }
+        if (COUNT && remaining > 0) cnt.rounds++;
+        bool active = remaining > 0;
+        int64_t keys[K];
+        float d2[K];
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            keys[s] = kEmptyKeyDesc;
+            d2[s] = 0.f;
+        }
+        int64_t floor_key = -1;
+        const float thi = key_t(hi_key);
+        bool stop = false;
+        auto replay_front = [&]() {
+            const int64_t key = keys[0];
+            const int j = key_j(key);
+            const float4 g0 = __ldg(rec + 4 * j + 0);
+            const float4 g1 = __ldg(rec + 4 * j + 1);
+            const float4 g2 = __ldg(rec + 4 * j + 2);
+            const float4 sh = __ldg(rec + 4 * j + 3);
+            Hit h;
+            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+            const float e = expf(__fmul_rn(-0.5f, h.D2));
+            const float a = __fmul_rn(sh.x, e);
+            const float om = __fsub_rn(1.f, a);
+            const float Ti = __fdiv_rn(Tn, om);
+            const float w = Ti * a;
+            const float dLda =
+                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
+            U0 = fmaf(a, sh.y, om * U0);
+            U1 = fmaf(a, sh.z, om * U1);
+            U2 = fmaf(a, sh.w, om * U2);
+            UA = fmaf(om, UA, a);
+            Tn = Ti;
+            const float gD2 = -0.5f * a * dLda;
+            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
+            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            float4* gp = gtmp + 4 * j;
+            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
+            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
+            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
+            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+            --remaining;
+            hi_key = key;
+            if (COUNT) cnt.hits++;
+            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+        };
+        auto drop_floor = [&](float x) {  // a node with packet exit x was dropped for this pass
+            if (active) floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
+        };
+        WarpQueue q;
+        wq_init<true>(q);
+        wq_push<true>(q, INF, 0, lane);
+        int visits = 0;
+        while (true) {
+            float x_node;
+            int node;
+            if (!wq_pop<true>(q, x_node, node, lane)) break;
+            bool need = false;
+            if (active) {
+                const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                const bool full = keys[K - 1] != kEmptyKeyDesc;
+                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                if (x_node >= tfl) {
+                    if (x_node < tK) floor_key = max(floor_key, pack_key(fmaxf(x_node, 0.f), kFloorJ));
+                    else need = true;
+                }
+            }
+            if (__any_sync(FULL, need)) {
+                if (++visits > P.max_visits) {
+                    if (lane == 0) atomicOr(err, kErrLoopGuard);
+                    stop = true;
+                    break;
+                }
+                const float4 n0 = __ldg(nodes + 4 * node + 0);
+                const float4 n1 = __ldg(nodes + 4 * node + 1);
+                const float4 n2 = __ldg(nodes + 4 * node + 2);
+                const float4 n3 = __ldg(nodes + 4 * node + 3);
+                if (COUNT && need) cnt.nodes++;
+                float en0, ex0, en1, ex1;
+                slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
+                const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+                const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
+                bool h0 = false, h1 = false;
+                if (need) {
+                    const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                    const bool full = keys[K - 1] != kEmptyKeyDesc;
+                    const float tK = full ? key_t(keys[K - 1]) : NINF;
+                    h0 = en0 <= thi && ex0 >= tfl && ex0 >= en0;
+                    h1 = en1 <= thi && ex1 >= tfl && ex1 >= en1;
+                    if (h0 && ex0 < tK) { h0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                    if (h1 && ex1 < tK) { h1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+                }
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int rr = side ? r1 : r0;
+                    const bool want = (side ? h1 : h0) && rr < 0;
+                    if (__any_sync(FULL, want)) {
+                        const int start = ~rr, num = side ? c1 : c0;
+                        for (int qq = start; qq < start + num; ++qq) {
+                            if (want) {
+                                const float4 g0 = __ldg(rec + 4 * qq + 0);
+                                const float4 g1 = __ldg(rec + 4 * qq + 1);
+                                const float4 g2 = __ldg(rec + 4 * qq + 2);
+                                Hit h;
+                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                                if (COUNT) cnt.tests++;
+                                if (h.hit) {
+                                    const int64_t key = pack_key(h.t1, qq);
+                                    if (key < hi_key && key > floor_key) {
+                                        if (key > keys[K - 1]) {
+                                            if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
+                                            kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                            if (COUNT) cnt.inserted++;
+                                        } else {
+                                            floor_key = key;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+                bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+                if (need) {
+                    const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
+                    const bool full = keys[K - 1] != kEmptyKeyDesc;
+                    const float tK = full ? key_t(keys[K - 1]) : NINF;
+                    if (i0 && ex0 < tfl) i0 = false;
+                    if (i1 && ex1 < tfl) i1 = false;
+                    if (i0 && ex0 < tK) { i0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
+                    if (i1 && ex1 < tK) { i1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+                }
+                if (__any_sync(FULL, i0)) {
+                    const float xp = warp_max(i0 ? ex0 : NINF);
+                    if (!wq_push<true>(q, xp, r0, lane)) drop_floor(xp);
+                }
+                if (__any_sync(FULL, i1)) {
+                    const float xp = warp_max(i1 ? ex1 : NINF);
+                    if (!wq_push<true>(q, xp, r1, lane)) drop_floor(xp);
+                }
+            }
+            const float bound = wq_top<true>(q);
+            while (active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound) replay_front();
+            active = active && remaining > 0;
+            if (!__any_sync(FULL, active)) break;
+        }
+        if (__any_sync(FULL, stop)) break;
+        while (active && remaining > 0 && keys[0] != kEmptyKeyDesc) replay_front();
+        if (active && remaining > 0 && floor_key < 0) {
+            atomicOr(err, kErrReplayMismatch);
+            remaining = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int lane, DevCam& cam, int& px, int& py,
@@ -500,7 +1338,7 @@ __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int l
     return px < cam.W && py < cam.H && ty < cam.tiles_y;
 }
 
-template <int K, bool PERSIST, bool COUNT>
+template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -516,13 +1354,21 @@ __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
         DevCam cam;
         int px, py;
         int64_t pix;
-        if (tile_pixel(A, tile, lane, cam, px, py, pix)) {
-            float3 o, d;
-            camera_ray(cam, px, py, o, d);
-            float C0, C1, C2, T, depth;
-            int64_t last_key;
-            int count;
+        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
+        float C0, C1, C2, T, depth;
+        int64_t last_key;
+        int count;
+        float3 o, d;
+        camera_ray(cam, px, py, o, d);
+        if (MODE == 2)
+            trace_forward_bf<K, COUNT>(A.rec, A.nodes, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count, cnt,
+                                       A.err);
+        else if (MODE == 1)
+            trace_forward_packet<K, COUNT>(A.rec, A.nodes, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+                                           cnt, A.err);
+        else if (valid)
             trace_forward<K, COUNT>(A.rec, A.nodes, A.P, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
+        if (valid) {
             A.rgb[3 * pix + 0] = fmaf(T, A.P.bg[0], C0);
             A.rgb[3 * pix + 1] = fmaf(T, A.P.bg[1], C1);
             A.rgb[3 * pix + 2] = fmaf(T, A.P.bg[2], C2);
@@ -549,7 +1395,7 @@ __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
     }
 }
 
-template <int K, bool PERSIST, bool COUNT>
+template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -565,18 +1411,28 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
         DevCam cam;
         int px, py;
         int64_t pix;
-        if (tile_pixel(A, tile, lane, cam, px, py, pix)) {
-            const int n = A.sn[pix];
-            if (n > 0) {
-                float3 o, d;
-                camera_ray(cam, px, py, o, d);
-                const float gC[3] = {B.d_rgb[3 * pix], B.d_rgb[3 * pix + 1], B.d_rgb[3 * pix + 2]};
-                const float gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
-                trace_backward<K, COUNT>(A.rec, A.nodes, A.P, o, d, A.sT[pix], A.skey[pix], n, gC, gA, B.gtmp, cnt,
-                                         A.err);
-                if (COUNT) ++rays;
-            }
+        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
+        const int n = valid ? A.sn[pix] : 0;
+        float3 o, d;
+        camera_ray(cam, px, py, o, d);
+        float gC[3] = {0.f, 0.f, 0.f};
+        float gA = 0.f, Tf = 1.f;
+        int64_t lk = -1;
+        if (n > 0) {
+            gC[0] = B.d_rgb[3 * pix];
+            gC[1] = B.d_rgb[3 * pix + 1];
+            gC[2] = B.d_rgb[3 * pix + 2];
+            gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
+            Tf = A.sT[pix];
+            lk = A.skey[pix];
+            if (COUNT) ++rays;
         }
+        if (MODE == 2)
+            trace_backward_bf<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+        else if (MODE == 1)
+            trace_backward_packet<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+        else if (n > 0)
+            trace_backward<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         if (!PERSIST) break;
     }
     if (COUNT) {
@@ -689,79 +1545,74 @@ __global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs
 // ---------------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------------
-template <int K, bool PERSIST, bool COUNT>
-static cudaError_t launch_fwd_k(const FwdArgs& A, int grid, int block, cudaStream_t st) {
-    k_render_fwd<K, PERSIST, COUNT><<<grid, block, 0, st>>>(A);
-    return cudaGetLastError();
-}
-
-template <int K, bool PERSIST>
-static int occupancy_fwd(int block, bool count) {
+template <int K, bool PERSIST, bool COUNT, int MODE>
+static int occupancy_of(bool backward, int block) {
     int nb = 0;
-    if (count)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, true>, block, 0);
+    if (backward)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, COUNT, MODE>, block, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, false>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, COUNT, MODE>, block, 0);
     return nb;
 }
 
-template <int K, bool PERSIST>
-static int occupancy_bwd(int block, bool count) {
-    int nb = 0;
-    if (count)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, true>, block, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, false>, block, 0);
-    return nb;
+template <int K, bool COUNT>
+static int occupancy_m(bool backward, int block, int mode) {
+    if (mode == 2) return occupancy_of<K, true, COUNT, 2>(backward, block);
+    if (mode == 1) return occupancy_of<K, true, COUNT, 1>(backward, block);
+    return occupancy_of<K, true, COUNT, 0>(backward, block);
 }
 
-int persistent_grid(bool backward, int K, int block, bool count, int sms) {
+int persistent_grid(bool backward, int K, int block, bool count, int mode, int sms) {
     int nb = 1;
-    if (!backward) {
-        if (K == 8) nb = occupancy_fwd<8, true>(block, count);
-        else if (K == 16) nb = occupancy_fwd<16, true>(block, count);
-        else nb = occupancy_fwd<32, true>(block, count);
-    } else {
-        if (K == 8) nb = occupancy_bwd<8, true>(block, count);
-        else if (K == 16) nb = occupancy_bwd<16, true>(block, count);
-        else nb = occupancy_bwd<32, true>(block, count);
-    }
+    if (K == 8) nb = count ? occupancy_m<8, true>(backward, block, mode) : occupancy_m<8, false>(backward, block, mode);
+    else if (K == 16)
+        nb = count ? occupancy_m<16, true>(backward, block, mode) : occupancy_m<16, false>(backward, block, mode);
+    else nb = count ? occupancy_m<32, true>(backward, block, mode) : occupancy_m<32, false>(backward, block, mode);
     return std::max(1, nb) * sms;
 }
 
-cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int grid, int block, cudaStream_t st) {
-#define RS_FWD(KK)                                                                   \
-    if (K == KK) {                                                                   \
-        if (persistent) return count ? launch_fwd_k<KK, true, true>(A, grid, block, st)   \
-                                     : launch_fwd_k<KK, true, false>(A, grid, block, st); \
-        return count ? launch_fwd_k<KK, false, true>(A, grid, block, st)                  \
-                     : launch_fwd_k<KK, false, false>(A, grid, block, st);                \
-    }
-    RS_FWD(8)
-    RS_FWD(16)
-    RS_FWD(32)
-#undef RS_FWD
-    return cudaErrorInvalidValue;
+template <int K, bool PERSIST, bool COUNT, int MODE>
+static void launch_one(bool backward, const FwdArgs& A, const BwdArgs* B, int grid, int block, cudaStream_t st) {
+    if (backward) k_render_bwd<K, PERSIST, COUNT, MODE><<<grid, block, 0, st>>>(A, *B);
+    else k_render_fwd<K, PERSIST, COUNT, MODE><<<grid, block, 0, st>>>(A);
 }
 
-cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int grid,
-                            int block, cudaStream_t st) {
-#define RS_BWD(KK)                                                                                   \
-    if (K == KK) {                                                                                   \
-        if (persistent) {                                                                            \
-            if (count) k_render_bwd<KK, true, true><<<grid, block, 0, st>>>(A, B);                    \
-            else k_render_bwd<KK, true, false><<<grid, block, 0, st>>>(A, B);                         \
-        } else {                                                                                     \
-            if (count) k_render_bwd<KK, false, true><<<grid, block, 0, st>>>(A, B);                   \
-            else k_render_bwd<KK, false, false><<<grid, block, 0, st>>>(A, B);                        \
-        }                                                                                            \
-        return cudaGetLastError();                                                                   \
+template <int K, bool PERSIST, bool COUNT>
+static void launch_mode(bool backward, const FwdArgs& A, const BwdArgs* B, int mode, int grid, int block,
+                        cudaStream_t st) {
+    if (mode == 2) launch_one<K, PERSIST, COUNT, 2>(backward, A, B, grid, block, st);
+    else if (mode == 1) launch_one<K, PERSIST, COUNT, 1>(backward, A, B, grid, block, st);
+    else launch_one<K, PERSIST, COUNT, 0>(backward, A, B, grid, block, st);
+}
+
+template <int K>
+static void launch_kp(bool backward, const FwdArgs& A, const BwdArgs* B, bool persistent, bool count, int mode,
+                      int grid, int block, cudaStream_t st) {
+    if (persistent) {
+        if (count) launch_mode<K, true, true>(backward, A, B, mode, grid, block, st);
+        else launch_mode<K, true, false>(backward, A, B, mode, grid, block, st);
+    } else {
+        if (count) launch_mode<K, false, true>(backward, A, B, mode, grid, block, st);
+        else launch_mode<K, false, false>(backward, A, B, mode, grid, block, st);
     }
-    RS_BWD(8)
-    RS_BWD(16)
-    RS_BWD(32)
-#undef RS_BWD
-    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,
+                           cudaStream_t st) {
+    if (K == 8) launch_kp<8>(false, A, nullptr, persistent, count, mode, grid, block, st);
+    else if (K == 16) launch_kp<16>(false, A, nullptr, persistent, count, mode, grid, block, st);
+    else if (K == 32) launch_kp<32>(false, A, nullptr, persistent, count, mode, grid, block, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
+                            int grid, int block, cudaStream_t st) {
+    if (K == 8) launch_kp<8>(true, A, &B, persistent, count, mode, grid, block, st);
+    else if (K == 16) launch_kp<16>(true, A, &B, persistent, count, mode, grid, block, st);
+    else if (K == 32) launch_kp<32>(true, A, &B, persistent, count, mode, grid, block, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,

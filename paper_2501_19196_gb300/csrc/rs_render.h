@@ -36,11 +36,11 @@ struct BwdArgs {
     float4* gtmp;  // 4 per Gaussian (Morton order): (dM row k, dm_k) k = 0..2, (dop, drgb)
 };
 
-int persistent_grid(bool backward, int K, int block, bool count, int sms);
-cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int grid, int block,
+int persistent_grid(bool backward, int K, int block, bool count, int mode, int sms);
+cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,
                            cudaStream_t st);
-cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int grid,
-                            int block, cudaStream_t st);
+cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
+                            int grid, int block, cudaStream_t st);
 cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,
                             const float* scales, int64_t n, const rs_gaussian_grads& out, cudaStream_t st);
 cudaError_t launch_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px,
@@ -69,6 +69,7 @@ struct rs_fwd_state {
     int64_t total_tiles = 0;
     int tile_w = 8, kbuf = 16, block_warps = 4;
     int persistent = 1;
+    int traversal = 1;
     const rs_accel* accel = nullptr;
     int64_t n_gauss = 0;
 };

@@ -23,12 +23,12 @@ def default_cache_path() -> str:
     return os.environ.get(CACHE_ENV, os.path.join(os.path.expanduser("~"), ".cache", "raysplats_tune.json"))
 
 
-def candidates(tiles=((8, 4), (4, 8), (16, 2)), kbufs=(8, 16, 32), leaves=(2, 4, 8), warps=(2, 4),
-               persistent=1, morton_bits=21):
+def candidates(tiles=((8, 4), (4, 8)), kbufs=(8, 16, 32), leaves=(1, 2, 4), warps=(4,), morton=(20, 21),
+               traversal=(1,), persistent=1):
+    """The cross product of the given tunables (all persistent launches by default)."""
     out = []
-    for (tw, th), k, leaf, w in itertools.product(tiles, kbufs, leaves, warps):
-        t = native.RsTuneParams(tw, th, k, leaf, morton_bits, persistent, w)
-        out.append(t)
+    for (tw, th), k, leaf, w, mb, tr in itertools.product(tiles, kbufs, leaves, warps, morton, traversal):
+        out.append(native.RsTuneParams(tw, th, k, leaf, mb, persistent, w, tr))
     return out
 
 

@@ -64,7 +64,8 @@ def test_host_validation_rejects_bad_arguments(lib):
         native.RS_ERR_INVALID_ARG
     # bad tile / kbuf / leaf / Q_box
     g = native.RsGaussians(10, 16, 16, 16, 16, 16)
-    for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("morton_bits", 7), ("block_warps", 9)):
+    for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("morton_bits", 7), ("block_warps", 9),
+                       ("traversal", 2)):
         bad = native.default_tune(**{field: val})
         if field == "tile_w":
             bad.tile_h = 10

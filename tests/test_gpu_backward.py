@@ -79,7 +79,9 @@ def test_gradients_invariant_to_tunables():
     cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 40, 24, 55.0),
                                   scenes.look_at_camera((2.0, 2.0, -2.0), (0, 0, 0), 16, 40, 50.0)])
     prm = params(eps1=1e-3)
-    for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16)):
+    for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16),
+               dict(traversal=0), dict(traversal=0, kbuf=8, leaf_size=1), dict(traversal=2),
+               dict(traversal=2, kbuf=8, leaf_size=1)):
         errs, _ = _grad_case(sc, cams, prm, tune=native.default_tune(**kw))
         assert max(errs.values()) < TOL_GRAD, (kw, errs)
 

@@ -226,7 +226,8 @@ def test_tunables_and_launch_modes_bit_identical():
     ref = gpu_render(sc, cams, prm, tune=native.default_tune())
     for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(leaf_size=8), dict(leaf_size=16),
                dict(tile_w=4), dict(tile_w=16), dict(tile_w=32), dict(persistent=0), dict(morton_bits=10),
-               dict(morton_bits=20),
+               dict(morton_bits=20), dict(traversal=0), dict(traversal=0, leaf_size=1, kbuf=8),
+               dict(traversal=2), dict(traversal=2, leaf_size=1, kbuf=8), dict(traversal=2, persistent=0),
                dict(block_warps=1), dict(block_warps=2)):
         out = gpu_render(sc, cams, prm, tune=native.default_tune(**kw))
         for k in ("rgb", "alpha", "depth"):
