@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--kbuf", type=int, default=None)
     p.add_argument("--leaf", type=int, default=None)
     p.add_argument("--tile-w", type=int, default=None)
+    p.add_argument("--traversal", type=int, default=None)
+    p.add_argument("--smem-nodes", type=int, default=None)
     p.add_argument("--profile", action="store_true",
                    help="ncu mode: `warmup` eager batched steps, then one more step, then exit (no JSON)")
     return p.parse_args()
@@ -238,6 +240,10 @@ def run_ours(args):
         overrides["leaf_size"] = args.leaf
     if args.tile_w:
         overrides["tile_w"] = args.tile_w
+    if args.traversal is not None:
+        overrides["traversal"] = args.traversal
+    if args.smem_nodes is not None:
+        overrides["smem_nodes"] = args.smem_nodes
     tune_b = native.default_tune(persistent=1, **overrides)
     tune_p = native.default_tune(persistent=0, **overrides)
     n = wl.scene.n
@@ -423,7 +429,8 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{nr} stratified rays of the same workload, fwd + gradient, FP64 brute force, {dt:.1f} s"}
 
-    launches_build = 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3
+    # bounds init, bounds, morton, 3 per sort pass, records, karras, refit, top-node staging
+    launches_build = 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3 + (1 if tune_b.smem_nodes > 0 else 0)
     gpu_launches = args.steps * (launches_build + 1 + 2)
     value = P / ms_fb / 1e3 * world
     line = {

@@ -134,7 +134,9 @@ typedef struct {
  *   traversal       0: each lane traverses its own ray (depth first); 1: the 32 rays of a
  *                   tile traverse as a warp packet (shared node sequence, per-ray state, depth
  *                   first); 2: warp packet in best-first order of box entry (a priority queue
- *                   distributed over the warp's registers) */
+ *                   distributed over the warp's registers)
+ *   smem_nodes      0..512: the top BVH nodes (breadth first) that rs_build_accel stages for
+ *                   the render kernels' shared memory (64 B each); 0 disables staging */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t kbuf;
@@ -143,6 +145,7 @@ typedef struct {
     int32_t persistent;
     int32_t block_warps;
     int32_t traversal;
+    int32_t smem_nodes;
 } rs_tune_params;
 
 typedef struct rs_accel rs_accel;
@@ -165,8 +168,8 @@ int32_t rs_abi_version(void);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rs_last_error(void);
 
-/* Fill *out with the default tunables (8x4 tiles, kbuf 16, leaf 4, 63-bit codes,
- * persistent launch, 4 warps per CTA, warp-packet traversal). */
+/* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 8, 63-bit codes,
+ * persistent launch, 4 warps per CTA, best-first warp-packet traversal, 256 staged nodes). */
 rs_status rs_default_tune(rs_tune_params* out);
 
 /* Build the acceleration structure of a scene (LBVH): per-Gaussian render records

@@ -64,6 +64,8 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
         return set_error(RS_ERR_INVALID_ARG, "morton_bits %d: must be 10, 20 (extended) or 21", t->morton_bits);
     if (t->block_warps < 1 || t->block_warps > 4)
         return set_error(RS_ERR_INVALID_ARG, "block_warps %d: must be 1..4", t->block_warps);
+    if (t->smem_nodes < 0 || t->smem_nodes > kMaxSmemNodes)
+        return set_error(RS_ERR_INVALID_ARG, "smem_nodes %d: must be 0..%d", t->smem_nodes, kMaxSmemNodes);
     if (t->traversal < 0 || t->traversal > 2)
         return set_error(RS_ERR_INVALID_ARG, "traversal %d: must be 0 (per ray), 1 (warp packet) or 2 (best-first "
                          "warp packet)", t->traversal);
@@ -95,12 +97,13 @@ rs_status rs_default_tune(rs_tune_params* out) {
     if (!out) return set_error(RS_ERR_INVALID_ARG, "out is NULL");
     out->tile_w = 8;
     out->tile_h = 4;
-    out->kbuf = 16;
-    out->leaf_size = 4;
+    out->kbuf = 32;
+    out->leaf_size = 8;
     out->morton_bits = 21;
     out->persistent = 1;
     out->block_warps = 4;
-    out->traversal = 1;
+    out->traversal = 2;
+    out->smem_nodes = 256;
     return RS_OK;
 }
 
@@ -118,7 +121,7 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
         A = new (std::nothrow) rs_accel();
         if (!A) return set_error(RS_ERR_OOM, "host allocation failed");
         cudaGetDevice(&A->device);
-        if ((st = dmalloc(A->bounds, 6)) || (st = dmalloc(A->err, 1))) {
+        if ((st = dmalloc(A->bounds, 6)) || (st = dmalloc(A->err, 1)) || (st = dmalloc(A->top, 4 * kMaxSmemNodes))) {
             delete A;
             return st;
         }
@@ -129,7 +132,7 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
     if (n > A->cap) {
         const int64_t cap = n;
         const int64_t nb = (cap + 2047) / 2048;
-        if ((st = dmalloc(A->rec, 4 * cap)) || (st = dmalloc(A->pbox, 6 * cap)) ||
+        if ((st = dmalloc(A->rec, 4 * cap)) || (st = dmalloc(A->pbox, 6 * cap)) || (st = dmalloc(A->sph, cap)) ||
             (st = dmalloc(A->keys[0], cap)) || (st = dmalloc(A->keys[1], cap)) || (st = dmalloc(A->vals[0], cap)) ||
             (st = dmalloc(A->vals[1], cap)) || (st = dmalloc(A->hist, 256 * nb)) || (st = dmalloc(A->left, cap)) ||
             (st = dmalloc(A->right, cap)) || (st = dmalloc(A->first, cap)) || (st = dmalloc(A->last, cap)) ||
@@ -265,7 +268,10 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
 
     FwdArgs A{};
     A.rec = accel->rec;
+    A.sph = accel->sph;
     A.nodes = accel->nodes;
+    A.top = accel->top;
+    A.n_top = accel->n_top;
     A.cams = S->cams_dev;
     A.n_cams = n_cams;
     A.tile_w = tw;
@@ -286,7 +292,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         A.total_tiles = tiles;
         if (cudaMemsetAsync(S->queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return cuda_check("queue reset");
         const int grid = (int)std::min<int64_t>(
-            persistent_grid(false, tune->kbuf, block, count, tune->traversal, sm_count()),
+            persistent_grid(false, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
             (tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_forward(A, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                              block, s);
@@ -343,7 +349,10 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         return cuda_check("gradient scratch reset");
     FwdArgs A{};
     A.rec = accel->rec;
+    A.sph = accel->sph;
     A.nodes = accel->nodes;
+    A.top = accel->top;
+    A.n_top = accel->n_top;
     A.cams = S->cams_dev;
     A.n_cams = S->n_cams;
     A.tile_w = S->tile_w;
@@ -363,7 +372,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         if (cudaMemsetAsync(S->queue + 1, 0, sizeof(unsigned long long), s) != cudaSuccess)
             return cuda_check("queue reset");
         const int grid = (int)std::min<int64_t>(
-            persistent_grid(true, tune->kbuf, block, count, tune->traversal, sm_count()),
+            persistent_grid(true, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
             (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                               block, s);
@@ -400,9 +409,9 @@ rs_status rs_render_backward_counted(const rs_gaussians* g, const rs_accel* acce
 rs_status rs_accel_destroy(rs_accel* A) {
     if (!A) return RS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {A->rec,  A->pbox,  A->keys[0], A->keys[1], A->vals[0], A->vals[1], A->hist,   A->bounds,
+    void* ptrs[] = {A->rec,  A->pbox,  A->sph, A->keys[0], A->keys[1], A->vals[0], A->vals[1], A->hist,   A->bounds,
                     A->left, A->right, A->first,   A->last,    A->parent,  A->nbox,    A->counter, A->nodes,
-                    A->err};
+                    A->top,  A->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;

@@ -236,7 +236,8 @@ __device__ __forceinline__ void quat_rot(float qa, float qb, float qc, float qd,
 __global__ void k_records(const float* __restrict__ means, const float* __restrict__ quats,
                           const float* __restrict__ scales, const float* __restrict__ opac,
                           const float* __restrict__ rgb, const uint32_t* __restrict__ perm, int64_t n,
-                          float Q, float4* __restrict__ rec, float* __restrict__ pbox, int* err) {
+                          float Q, float4* __restrict__ rec, float* __restrict__ pbox, float4* __restrict__ sph,
+                          int* err) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int64_t i = perm[j];
@@ -269,6 +270,10 @@ __global__ void k_records(const float* __restrict__ means, const float* __restri
         pbox[6 * j + a] = m[a] - ext;
         pbox[6 * j + 3 + a] = m[a] + ext;
     }
+    // bounding sphere of the ellipsoid: radius sqrt(Q) * max scale, padded like the box
+    const float smax = fmaxf(fmaxf(s[0], s[1]), s[2]);
+    const float r = (sq * smax) * (1.f + 1e-5f) + 1e-30f;
+    sph[j] = make_float4(m[0], m[1], m[2], r * r);
     if (bad) atomicOr(err, kErrBadScene);
 }
 
@@ -383,6 +388,73 @@ __global__ void k_refit(int64_t n, const int* __restrict__ left, const int* __re
     }
 }
 
+// Breadth-first staging of the top `m` nodes for the render kernels' shared memory.  Slots are
+// assigned level by level in node order (deterministic: a block scan over the children
+// counts); each staged copy refers to its staged children as kTopRef + slot.  One CTA.
+__global__ void __launch_bounds__(kMaxSmemNodes) k_stage_top(const float4* __restrict__ nodes, int m,
+                                                             float4* __restrict__ top) {
+    __shared__ int cur[kMaxSmemNodes], nxt[kMaxSmemNodes], pos[kMaxSmemNodes];
+    __shared__ int n_cur, n_next, base_next;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        cur[0] = 0;
+        n_cur = 1;
+    }
+    __syncthreads();
+    int base = 0;  // slot of cur[0]
+    while (true) {
+        const int nc = n_cur;
+        if (nc == 0) break;
+        float4 n0, n1, n2, n3;
+        int cnt = 0;
+        if (t < nc) {
+            const int node = cur[t];
+            n0 = nodes[4 * node];
+            n1 = nodes[4 * node + 1];
+            n2 = nodes[4 * node + 2];
+            n3 = nodes[4 * node + 3];
+            cnt = (__float_as_int(n3.x) >= 0) + (__float_as_int(n3.y) >= 0);
+        }
+        pos[t] = cnt;
+        __syncthreads();
+        for (int off = 1; off < kMaxSmemNodes; off <<= 1) {  // inclusive scan of the counts
+            const int v = t >= off ? pos[t - off] : 0;
+            __syncthreads();
+            pos[t] += v;
+            __syncthreads();
+        }
+        if (t == 0) {
+            base_next = base + nc;
+            n_next = min(pos[kMaxSmemNodes - 1], max(0, m - (base + nc)));
+        }
+        __syncthreads();
+        if (t < nc) {
+            int r[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};
+            int p = pos[t] - cnt;  // exclusive position of this node's first internal child
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (r[c] >= 0) {
+                    if (p < n_next) {
+                        nxt[p] = r[c];
+                        r[c] = kTopRef + base_next + p;
+                    }
+                    ++p;
+                }
+            }
+            const int slot = base + t;
+            top[4 * slot] = n0;
+            top[4 * slot + 1] = n1;
+            top[4 * slot + 2] = n2;
+            top[4 * slot + 3] = make_float4(__int_as_float(r[0]), __int_as_float(r[1]), n3.z, n3.w);
+        }
+        __syncthreads();
+        if (t < n_next) cur[t] = nxt[t];
+        if (t == 0) n_cur = n_next;
+        base = base_next;
+        __syncthreads();
+    }
+}
+
 // single Gaussian: a root whose first child is the leaf and whose second child is empty
 __global__ void k_single_root(const float* __restrict__ pbox, float4* __restrict__ nodes) {
     const float* b = pbox;
@@ -417,7 +489,7 @@ rs_status build_accel_device(Accel& A, const rs_gaussians& g, const rs_tune_para
     }
     // passes is even: the sorted (code, id) pairs are back in buffer 0
     k_records<<<grid_for(n, 256), 256, 0, st>>>(g.means, g.quats, g.scales, g.opacities, g.rgb, A.vals[0], n,
-                                               A.Q_box, A.rec, A.pbox, A.err);
+                                               A.Q_box, A.rec, A.pbox, A.sph, A.err);
     if (n == 1) {
         k_single_root<<<1, 1, 0, st>>>(A.pbox, A.nodes);
     } else {
@@ -426,6 +498,10 @@ rs_status build_accel_device(Accel& A, const rs_gaussians& g, const rs_tune_para
         k_refit<<<grid_for(n, 256), 256, 0, st>>>(n, A.left, A.right, A.first, A.last, A.parent, A.pbox, A.nbox,
                                                  A.counter, A.nodes, tp.leaf_size, A.err);
     }
+    // at most one node per internal node can be staged (n - 1 internal nodes, one for n == 1)
+    A.n_top = (int)std::min<int64_t>(std::min(tp.smem_nodes, kMaxSmemNodes), std::max<int64_t>(1, n - 1));
+    if (tp.smem_nodes <= 0) A.n_top = 0;
+    if (A.n_top > 0) k_stage_top<<<1, kMaxSmemNodes, 0, st>>>(A.nodes, A.n_top, A.top);
     return cuda_check("rs_build_accel launch");
 }
 

@@ -32,6 +32,41 @@ __device__ __forceinline__ float safe_rcp(float x) {
     return __frcp_rn(ax > 1e-30f ? x : copysignf(1e-30f, x));
 }
 
+// Cheap conservative rejection before the full ray/ellipsoid solve: the ray must pass within
+// the Gaussian's bounding sphere (radius sqrt(Q) * max scale, padded).  The squared distance
+// |w|^2 - <w, d>^2 is widened by 1e-6 |w|^2 to absorb its rounding, so a ray the solve would
+// accept is never rejected here.
+__device__ __forceinline__ bool sphere_may_hit(const float3 o, const float3 d, const float4 sp) {
+    const float wx = sp.x - o.x, wy = sp.y - o.y, wz = sp.z - o.z;
+    const float tc = fmaf(wz, d.z, fmaf(wy, d.y, wx * d.x));
+    const float w2 = fmaf(wz, wz, fmaf(wy, wy, wx * wx));
+    return fmaf(-tc, tc, w2) <= fmaf(1e-6f, w2, sp.w);
+}
+
+// Where nodes come from: the staged top nodes (shared memory, references kTopRef + slot) or
+// the node array in global memory.  `root` is kTopRef when the top is staged, else 0.
+struct NodeSrc {
+    const float4* __restrict__ g;
+    const float4* s;
+    int root;
+};
+
+__device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& n0, float4& n1, float4& n2,
+                                           float4& n3) {
+    if (node >= kTopRef) {
+        const float4* p = ns.s + 4 * (node - kTopRef);
+        n0 = p[0];
+        n1 = p[1];
+        n2 = p[2];
+        n3 = p[3];
+    } else {
+        n0 = __ldg(ns.g + 4 * node + 0);
+        n1 = __ldg(ns.g + 4 * node + 1);
+        n2 = __ldg(ns.g + 4 * node + 2);
+        n3 = __ldg(ns.g + 4 * node + 3);
+    }
+}
+
 // Entry and exit parameters of both children's boxes, widened by 1e-6 relative so that rounding
 // can never drop a box that holds a hit (the boxes themselves are padded too).
 __device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const float4 n2, const float3 o,
@@ -58,46 +93,33 @@ __device__ __forceinline__ void slab2(const float4 n0, const float4 n1, const fl
 
 // ascending buffer: keys[0] nearest; insert `key` (< keys[K-1]) by one bubble pass
 template <int K>
-__device__ __forceinline__ void kbuf_insert_asc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
+__device__ __forceinline__ void kbuf_insert_asc(int64_t (&keys)[K], int64_t key) {
     keys[K - 1] = key;
-    d2[K - 1] = D2;
 #pragma unroll
     for (int s = K - 1; s > 0; --s) {
-        const bool sw = keys[s] < keys[s - 1];
         const int64_t ka = keys[s - 1], kb = keys[s];
-        const float da = d2[s - 1], db = d2[s];
-        keys[s - 1] = sw ? kb : ka;
-        keys[s] = sw ? ka : kb;
-        d2[s - 1] = sw ? db : da;
-        d2[s] = sw ? da : db;
+        keys[s - 1] = min(ka, kb);
+        keys[s] = max(ka, kb);
     }
 }
 
 // descending buffer: keys[0] farthest; insert `key` (> keys[K-1])
 template <int K>
-__device__ __forceinline__ void kbuf_insert_desc(int64_t (&keys)[K], float (&d2)[K], int64_t key, float D2) {
+__device__ __forceinline__ void kbuf_insert_desc(int64_t (&keys)[K], int64_t key) {
     keys[K - 1] = key;
-    d2[K - 1] = D2;
 #pragma unroll
     for (int s = K - 1; s > 0; --s) {
-        const bool sw = keys[s] > keys[s - 1];
         const int64_t ka = keys[s - 1], kb = keys[s];
-        const float da = d2[s - 1], db = d2[s];
-        keys[s - 1] = sw ? kb : ka;
-        keys[s] = sw ? ka : kb;
-        d2[s - 1] = sw ? db : da;
-        d2[s] = sw ? da : db;
+        keys[s - 1] = max(ka, kb);
+        keys[s] = min(ka, kb);
     }
 }
 
 // drop keys[0] (the hit just composited / replayed)
 template <int K>
-__device__ __forceinline__ void kbuf_pop_front(int64_t (&keys)[K], float (&d2)[K], int64_t empty) {
+__device__ __forceinline__ void kbuf_pop_front(int64_t (&keys)[K], int64_t empty) {
 #pragma unroll
-    for (int s = 0; s < K - 1; ++s) {
-        keys[s] = keys[s + 1];
-        d2[s] = d2[s + 1];
-    }
+    for (int s = 0; s < K - 1; ++s) keys[s] = keys[s + 1];
     keys[K - 1] = empty;
 }
 
@@ -118,7 +140,7 @@ struct Counters {
 // last composited key -- so the composited sequence is always the exact sorted prefix.
 // ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
-__device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+__device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                               const TraceParams& P, const float3 o, const float3 d, float& C0,
                                               float& C1, float& C2, float& T, float& depth,
                                               int64_t& last_key, int& count, Counters& cnt, int* err) {
@@ -142,20 +164,21 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
         }
         if (COUNT) cnt.rounds++;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKey;
-            d2[s] = 0.f;
         }
         int64_t cap = kEmptyKey;  // hits must have key < cap (tightened on overflow)
         const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
-        int sp = 0, node = 0, visits = 0;
+        int sp = 0, node = nodes.root, visits = 0;
         auto composite_front = [&]() {
             const int64_t key = keys[0];
             const int j = key_j(key);
+            Hit hc;  // the same solve as at insertion time: the same bits
+            ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
+                                 P.t_near, hc);
             const float4 sh = __ldg(rec + 4 * j + 3);
-            const float a = response_alpha(sh.x, d2[0]);
+            const float a = response_alpha(sh.x, hc.D2);
             const float w = __fmul_rn(T, a);
             C0 = fmaf(w, sh.y, C0);
             C1 = fmaf(w, sh.z, C1);
@@ -166,7 +189,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
             last_key = key;
             if (COUNT) cnt.hits++;
             if (T < eps || count >= P.k_max) done = true;
-            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+            kbuf_pop_front<K>(keys, kEmptyKey);
         };
         while (true) {
             if (++visits > P.max_visits) {
@@ -174,10 +197,8 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                 done = true;
                 break;
             }
-            const float4 n0 = __ldg(nodes + 4 * node + 0);
-            const float4 n1 = __ldg(nodes + 4 * node + 1);
-            const float4 n2 = __ldg(nodes + 4 * node + 2);
-            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float4 n0, n1, n2, n3;
+            fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT) cnt.nodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -201,6 +222,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                 if (hs && rr < 0) {
                     const int start = ~rr, num = side ? c1 : c0;
                     for (int q = start; q < start + num; ++q) {
+                        if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
                         const float4 g0 = __ldg(rec + 4 * q + 0);
                         const float4 g1 = __ldg(rec + 4 * q + 1);
                         const float4 g2 = __ldg(rec + 4 * q + 2);
@@ -212,7 +234,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                             if (key > lo_key && key < cap) {
                                 if (key < keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];  // evicted
-                                    kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                    kbuf_insert_asc<K>(keys, key);
                                     if (COUNT) cnt.inserted++;
                                 } else {
                                     cap = key;  // rejected: buffer full of nearer hits
@@ -293,7 +315,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
 // composited hit are pruned.  Overflow is handled with a key floor and a further pass.
 // ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
-__device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+__device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                const TraceParams& P, const float3 o, const float3 d, float T_final,
                                                int64_t last_key, int n_hits, const float gC[3], float gA,
                                                float4* __restrict__ gtmp, Counters& cnt, int* err) {
@@ -315,15 +337,13 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
         }
         if (COUNT) cnt.rounds++;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKeyDesc;
-            d2[s] = 0.f;
         }
         int64_t floor_key = -1;  // hits must have key > floor_key (raised on overflow)
         const float thi = key_t(hi_key);
-        int sp = 0, node = 0, visits = 0;
+        int sp = 0, node = nodes.root, visits = 0;
         bool stop = false;
         auto replay_front = [&]() {
             const int64_t key = keys[0];
@@ -361,7 +381,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
-            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+            kbuf_pop_front<K>(keys, kEmptyKeyDesc);
         };
         while (true) {
             if (++visits > P.max_visits) {
@@ -369,10 +389,8 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                 stop = true;
                 break;
             }
-            const float4 n0 = __ldg(nodes + 4 * node + 0);
-            const float4 n1 = __ldg(nodes + 4 * node + 1);
-            const float4 n2 = __ldg(nodes + 4 * node + 2);
-            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float4 n0, n1, n2, n3;
+            fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT) cnt.nodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -395,6 +413,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                 if (hs && rr < 0) {
                     const int start = ~rr, num = side ? c1 : c0;
                     for (int q = start; q < start + num; ++q) {
+                        if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
                         const float4 g0 = __ldg(rec + 4 * q + 0);
                         const float4 g1 = __ldg(rec + 4 * q + 1);
                         const float4 g2 = __ldg(rec + 4 * q + 2);
@@ -406,7 +425,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                             if (key < hi_key && key > floor_key) {
                                 if (key > keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];  // evicted
-                                    kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                    kbuf_insert_desc<K>(keys, key);
                                     if (COUNT) cnt.inserted++;
                                 } else {
                                     floor_key = key;
@@ -481,6 +500,61 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
 }
 
 // ---------------------------------------------------------------------------------------------
+// Warp-aggregated gradient scatter (packet adjoints; the whole warp calls it, converged).
+// Each lane offers its 16-float contribution (dM rows + dm, dopacity + drgb) to the Gaussian
+// in Morton position j (j < 0: nothing).  Lanes holding a Gaussian nobody else holds issue
+// their four float4 atomics at once; lanes sharing a Gaussian are summed into the group's
+// lowest lane first (shuffles), which then issues one set of atomics for the group.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int j, const float4 (&v)[4]) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(FULL, j);
+    const bool mine = j >= 0;
+    const bool single = mine && __popc(peers) == 1;
+    if (single) {
+        float4* gp = gtmp + 4 * j;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(gp + k, v[k]);
+    }
+    unsigned todo = __ballot_sync(FULL, mine && !single);
+    while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const unsigned grp = __shfl_sync(FULL, peers, lead);
+        const bool in = (grp >> lane) & 1u;
+        const bool small = __popc(grp) <= 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 x = in ? v[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (small) {
+                // gather: the leader adds the other members' values one lane at a time
+                unsigned rest = grp & ~(1u << lead);
+                float4 acc = x;
+                while (rest) {
+                    const int src = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    acc.x += __shfl_sync(FULL, x.x, src);
+                    acc.y += __shfl_sync(FULL, x.y, src);
+                    acc.z += __shfl_sync(FULL, x.z, src);
+                    acc.w += __shfl_sync(FULL, x.w, src);
+                }
+                x = acc;
+            } else {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    x.x += __shfl_xor_sync(FULL, x.x, off);
+                    x.y += __shfl_xor_sync(FULL, x.y, off);
+                    x.z += __shfl_xor_sync(FULL, x.z, off);
+                    x.w += __shfl_xor_sync(FULL, x.w, off);
+                }
+            }
+            if (lane == lead) atomicAdd(gtmp + 4 * j + k, x);
+        }
+        todo &= ~grp;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Warp-packet variants.  The 32 lanes of a warp (one ray tile) traverse together: the node
 // sequence is shared (uniform loads are broadcast, descent is decided by warp votes: a child
 // is visited when any active lane needs it), while each lane keeps its own streaming state --
@@ -490,7 +564,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
 // tested, in an order that does not change what it composites.
 // ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
-__device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+__device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                      const TraceParams& P, bool valid, const float3 o,
                                                      const float3 d, float& C0, float& C1, float& C2, float& T,
                                                      float& depth, int64_t& last_key, int& count, Counters& cnt,
@@ -517,20 +591,21 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
         if (COUNT && !done) cnt.rounds++;
         bool active = !done;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKey;
-            d2[s] = 0.f;
         }
         int64_t cap = kEmptyKey;
         const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
-        int sp = 0, node = 0, visits = 0;
+        int sp = 0, node = nodes.root, visits = 0;
         auto composite_front = [&]() {
             const int64_t key = keys[0];
             const int j = key_j(key);
+            Hit hc;  // the same solve as at insertion time: the same bits
+            ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
+                                 P.t_near, hc);
             const float4 sh = __ldg(rec + 4 * j + 3);
-            const float a = response_alpha(sh.x, d2[0]);
+            const float a = response_alpha(sh.x, hc.D2);
             const float w = __fmul_rn(T, a);
             C0 = fmaf(w, sh.y, C0);
             C1 = fmaf(w, sh.z, C1);
@@ -541,7 +616,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
             last_key = key;
             if (COUNT) cnt.hits++;
             if (T < eps || count >= P.k_max) done = true;
-            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+            kbuf_pop_front<K>(keys, kEmptyKey);
         };
         while (true) {
             if (++visits > P.max_visits) {
@@ -549,10 +624,8 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                 done = true;
                 break;
             }
-            const float4 n0 = __ldg(nodes + 4 * node + 0);
-            const float4 n1 = __ldg(nodes + 4 * node + 1);
-            const float4 n2 = __ldg(nodes + 4 * node + 2);
-            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float4 n0, n1, n2, n3;
+            fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT && active) cnt.nodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -576,7 +649,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                 if (__any_sync(FULL, want)) {
                     const int start = ~rr, num = side ? c1 : c0;
                     for (int q = start; q < start + num; ++q) {
-                        if (want) {
+                        if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
                             const float4 g1 = __ldg(rec + 4 * q + 1);
                             const float4 g2 = __ldg(rec + 4 * q + 2);
@@ -588,7 +661,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                                 if (key > lo_key && key < cap) {
                                     if (key < keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
-                                        kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                        kbuf_insert_asc<K>(keys, key);
                                         if (COUNT) cnt.inserted++;
                                     } else {
                                         cap = key;
@@ -657,12 +730,12 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                     }
                 }
             }
+            // (bound is +inf once no node is left: everything pending is composited)
             while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
             active = active && !done;
             if (next < 0 || !__any_sync(FULL, active)) break;
             node = next;
         }
-        while (active && !done && keys[0] != kEmptyKey) composite_front();
         if (active && !done) {
             if (cap == kEmptyKey) done = true;
             else lo_key = last_key;
@@ -672,7 +745,8 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
 
 template <int K, bool COUNT>
 __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__ rec,
-                                                      const float4* __restrict__ nodes, const TraceParams& P,
+                                                      const float4* __restrict__ sph, const NodeSrc& nodes,
+                                                      const TraceParams& P,
                                                       const float3 o, const float3 d, float T_final,
                                                       int64_t last_key, int n_hits, const float gC[3], float gA,
                                                       float4* __restrict__ gtmp, Counters& cnt, int* err) {
@@ -695,17 +769,15 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
         if (COUNT && remaining > 0) cnt.rounds++;
         bool active = remaining > 0;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKeyDesc;
-            d2[s] = 0.f;
         }
         int64_t floor_key = -1;
         const float thi = key_t(hi_key);
-        int sp = 0, node = 0, visits = 0;
+        int sp = 0, node = nodes.root, visits = 0;
         bool stop = false;
-        auto replay_front = [&]() {
+        auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
             const float4 g0 = __ldg(rec + 4 * j + 0);
@@ -731,15 +803,26 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
             const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
             const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
             const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
-            float4* gp = gtmp + 4 * j;
-            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
-            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
-            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
-            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+            jout = j;
+            vout[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
+            vout[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
+            vout[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
+            vout[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
-            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+            kbuf_pop_front<K>(keys, kEmptyKeyDesc);
+        };
+        // warp-uniform replay: every lane takes part in the aggregated scatter
+        auto replay_while = [&](auto cond) {
+            while (true) {
+                const bool c = cond();
+                if (!__any_sync(0xffffffffu, c)) break;
+                int jout = -1;
+                float4 vout[4];
+                if (c) replay_contrib(jout, vout);
+                scatter_grad_warp(gtmp, jout, vout);
+            }
         };
         while (true) {
             if (++visits > P.max_visits) {
@@ -747,10 +830,8 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                 stop = true;
                 break;
             }
-            const float4 n0 = __ldg(nodes + 4 * node + 0);
-            const float4 n1 = __ldg(nodes + 4 * node + 1);
-            const float4 n2 = __ldg(nodes + 4 * node + 2);
-            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float4 n0, n1, n2, n3;
+            fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT && active) cnt.nodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -773,7 +854,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                 if (__any_sync(FULL, want)) {
                     const int start = ~rr, num = side ? c1 : c0;
                     for (int q = start; q < start + num; ++q) {
-                        if (want) {
+                        if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
                             const float4 g1 = __ldg(rec + 4 * q + 1);
                             const float4 g2 = __ldg(rec + 4 * q + 2);
@@ -785,7 +866,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                                 if (key < hi_key && key > floor_key) {
                                     if (key > keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
-                                        kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                        kbuf_insert_desc<K>(keys, key);
                                         if (COUNT) cnt.inserted++;
                                     } else {
                                         floor_key = key;
@@ -854,13 +935,13 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                     }
                 }
             }
-            while (active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound) replay_front();
+            // (bound is -inf once no node is left: everything pending is replayed)
+            replay_while([&] { return active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound; });
             active = active && remaining > 0;
             if (next < 0 || !__any_sync(FULL, active)) break;
             node = next;
         }
         if (__any_sync(FULL, stop)) break;
-        while (active && remaining > 0 && keys[0] != kEmptyKeyDesc) replay_front();
         if (active && remaining > 0 && floor_key < 0) {
             atomicOr(err, kErrReplayMismatch);
             remaining = 0;
@@ -911,6 +992,52 @@ __device__ __forceinline__ bool wq_push(WarpQueue& q, float pr, int node, int la
         }
     }
     return false;
+}
+
+// push with eviction: when the queue is full, the worst entry among the queue and the new one
+// (largest priority for the min-queue, smallest for the max-queue) is dropped; returns true and
+// its priority in *evicted when something was dropped.
+template <bool MAXQ>
+__device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, int lane, float& evicted) {
+    if (wq_push<MAXQ>(q, pr, node, lane)) return false;
+    // worst slot of the (full) queue
+    float v = q.pr[0];
+    int bs = 0;
+#pragma unroll
+    for (int s = 1; s < kQSlots; ++s) {
+        const bool worse = MAXQ ? (q.pr[s] < v) : (q.pr[s] > v);
+        if (worse) {
+            v = q.pr[s];
+            bs = s;
+        }
+    }
+    int id = lane * kQSlots + bs;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int oid = __shfl_xor_sync(0xffffffffu, id, off);
+        const bool worse = MAXQ ? (ov < v || (ov == v && oid < id)) : (ov > v || (ov == v && oid < id));
+        if (worse) {
+            v = ov;
+            id = oid;
+        }
+    }
+    const bool replace = MAXQ ? (v < pr) : (v > pr);
+    if (!replace) {
+        evicted = pr;  // the new entry is the worst: drop it
+        return true;
+    }
+    const int owner = id / kQSlots, slot = id % kQSlots;
+    if (lane == owner) {
+#pragma unroll
+        for (int s = 0; s < kQSlots; ++s)
+            if (slot == s) {
+                q.pr[s] = pr;
+                q.nd[s] = node;
+            }
+    }
+    evicted = v;
+    return true;
 }
 
 // extreme priority over the whole queue (uniform); empty value when the queue is empty
@@ -980,7 +1107,7 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 template <int K, bool COUNT>
-__device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+__device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                  const TraceParams& P, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
                                                  int64_t& last_key, int& count, Counters& cnt, int* err) {
@@ -1005,19 +1132,20 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         if (COUNT && !done) cnt.rounds++;
         bool active = !done;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKey;
-            d2[s] = 0.f;
         }
         int64_t cap = kEmptyKey;
         const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
         auto composite_front = [&]() {
             const int64_t key = keys[0];
             const int j = key_j(key);
+            Hit hc;  // the same solve as at insertion time: the same bits
+            ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
+                                 P.t_near, hc);
             const float4 sh = __ldg(rec + 4 * j + 3);
-            const float a = response_alpha(sh.x, d2[0]);
+            const float a = response_alpha(sh.x, hc.D2);
             const float w = __fmul_rn(T, a);
             C0 = fmaf(w, sh.y, C0);
             C1 = fmaf(w, sh.z, C1);
@@ -1028,22 +1156,29 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             last_key = key;
             if (COUNT) cnt.hits++;
             if (T < eps || count >= P.k_max) done = true;
-            kbuf_pop_front<K>(keys, d2, kEmptyKey);
+            kbuf_pop_front<K>(keys, kEmptyKey);
         };
         auto drop_cap = [&](float e) {  // a node with packet entry e was dropped for this pass
-            if (active) cap = min(cap, pack_key(fmaxf(e, 0.f), 0));
+            if (active) {
+                cap = min(cap, pack_key(fmaxf(e, 0.f), 0));
+                // pending hits at or beyond the new cap may be preceded by hits of the dropped
+                // subtree: give them back (the next pass finds them again)
+#pragma unroll
+                for (int s = 0; s < K; ++s)
+                    if (keys[s] >= cap) keys[s] = kEmptyKey;
+            }
         };
         WarpQueue q;
         wq_init<false>(q);
-        wq_push<false>(q, -INF, 0, lane);
+        wq_push<false>(q, -INF, nodes.root, lane);
         int visits = 0;
         while (true) {
             float e_node;
             int node;
-            if (!wq_pop<false>(q, e_node, node, lane)) break;
+            const bool popped = wq_pop<false>(q, e_node, node, lane);
             // a lane needs the node unless its (conservative) entry lies past its bounds
             bool need = false;
-            if (active) {
+            if (popped && active) {
                 const float tcap = cap == kEmptyKey ? INF : key_t(cap);
                 const bool full = keys[K - 1] != kEmptyKey;
                 const float tK = full ? key_t(keys[K - 1]) : INF;
@@ -1058,10 +1193,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     done = true;
                     break;
                 }
-                const float4 n0 = __ldg(nodes + 4 * node + 0);
-                const float4 n1 = __ldg(nodes + 4 * node + 1);
-                const float4 n2 = __ldg(nodes + 4 * node + 2);
-                const float4 n3 = __ldg(nodes + 4 * node + 3);
+                float4 n0, n1, n2, n3;
+                fetch_node(nodes, node, n0, n1, n2, n3);
                 if (COUNT && need) cnt.nodes++;
                 float en0, ex0, en1, ex1;
                 slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -1085,7 +1218,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = side ? c1 : c0;
                         for (int qq = start; qq < start + num; ++qq) {
-                            if (want) {
+                            if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
@@ -1097,7 +1230,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                     if (key > lo_key && key < cap) {
                                         if (key < keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
-                                            kbuf_insert_asc<K>(keys, d2, key, h.D2);
+                                            kbuf_insert_asc<K>(keys, key);
                                             if (COUNT) cnt.inserted++;
                                         } else {
                                             cap = key;
@@ -1118,21 +1251,21 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     if (i0 && e0 > tK) { i0 = false; cap = min(cap, pack_key(e0, 0)); }
                     if (i1 && e1 > tK) { i1 = false; cap = min(cap, pack_key(e1, 0)); }
                 }
+                float ev;
                 if (__any_sync(FULL, i0)) {
                     const float ep = warp_min(i0 ? e0 : INF);
-                    if (!wq_push<false>(q, ep, r0, lane)) drop_cap(ep);
+                    if (wq_push_evict<false>(q, ep, r0, lane, ev)) drop_cap(ev);
                 }
                 if (__any_sync(FULL, i1)) {
                     const float ep = warp_min(i1 ? e1 : INF);
-                    if (!wq_push<false>(q, ep, r1, lane)) drop_cap(ep);
+                    if (wq_push_evict<false>(q, ep, r1, lane, ev)) drop_cap(ev);
                 }
             }
-            const float bound = wq_top<false>(q);
+            const float bound = wq_top<false>(q);  // +inf when empty: composite everything pending
             while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
             active = active && !done;
-            if (!__any_sync(FULL, active)) break;
+            if (!popped || !__any_sync(FULL, active)) break;
         }
-        while (active && !done && keys[0] != kEmptyKey) composite_front();
         if (active && !done) {
             if (cap == kEmptyKey) done = true;
             else lo_key = last_key;
@@ -1141,7 +1274,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
 }
 
 template <int K, bool COUNT>
-__device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ nodes,
+__device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                   const TraceParams& P, const float3 o, const float3 d,
                                                   float T_final, int64_t last_key, int n_hits, const float gC[3],
                                                   float gA, float4* __restrict__ gtmp, Counters& cnt, int* err) {
@@ -1164,16 +1297,14 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         if (COUNT && remaining > 0) cnt.rounds++;
         bool active = remaining > 0;
         int64_t keys[K];
-        float d2[K];
 #pragma unroll
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKeyDesc;
-            d2[s] = 0.f;
         }
         int64_t floor_key = -1;
         const float thi = key_t(hi_key);
         bool stop = false;
-        auto replay_front = [&]() {
+        auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
             const float4 g0 = __ldg(rec + 4 * j + 0);
@@ -1199,29 +1330,45 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
             const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
             const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
-            float4* gp = gtmp + 4 * j;
-            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
-            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
-            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
-            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+            jout = j;
+            vout[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
+            vout[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
+            vout[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
+            vout[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
-            kbuf_pop_front<K>(keys, d2, kEmptyKeyDesc);
+            kbuf_pop_front<K>(keys, kEmptyKeyDesc);
+        };
+        // warp-uniform replay: every lane takes part in the aggregated scatter
+        auto replay_while = [&](auto cond) {
+            while (true) {
+                const bool c = cond();
+                if (!__any_sync(0xffffffffu, c)) break;
+                int jout = -1;
+                float4 vout[4];
+                if (c) replay_contrib(jout, vout);
+                scatter_grad_warp(gtmp, jout, vout);
+            }
         };
         auto drop_floor = [&](float x) {  // a node with packet exit x was dropped for this pass
-            if (active) floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
+            if (active) {
+                floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
+#pragma unroll
+                for (int s = 0; s < K; ++s)
+                    if (keys[s] <= floor_key) keys[s] = kEmptyKeyDesc;
+            }
         };
         WarpQueue q;
         wq_init<true>(q);
-        wq_push<true>(q, INF, 0, lane);
+        wq_push<true>(q, INF, nodes.root, lane);
         int visits = 0;
         while (true) {
             float x_node;
             int node;
-            if (!wq_pop<true>(q, x_node, node, lane)) break;
+            const bool popped = wq_pop<true>(q, x_node, node, lane);
             bool need = false;
-            if (active) {
+            if (popped && active) {
                 const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                 const bool full = keys[K - 1] != kEmptyKeyDesc;
                 const float tK = full ? key_t(keys[K - 1]) : NINF;
@@ -1236,10 +1383,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     stop = true;
                     break;
                 }
-                const float4 n0 = __ldg(nodes + 4 * node + 0);
-                const float4 n1 = __ldg(nodes + 4 * node + 1);
-                const float4 n2 = __ldg(nodes + 4 * node + 2);
-                const float4 n3 = __ldg(nodes + 4 * node + 3);
+                float4 n0, n1, n2, n3;
+                fetch_node(nodes, node, n0, n1, n2, n3);
                 if (COUNT && need) cnt.nodes++;
                 float en0, ex0, en1, ex1;
                 slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
@@ -1262,7 +1407,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = side ? c1 : c0;
                         for (int qq = start; qq < start + num; ++qq) {
-                            if (want) {
+                            if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
@@ -1274,7 +1419,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                     if (key < hi_key && key > floor_key) {
                                         if (key > keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
-                                            kbuf_insert_desc<K>(keys, d2, key, h.D2);
+                                            kbuf_insert_desc<K>(keys, key);
                                             if (COUNT) cnt.inserted++;
                                         } else {
                                             floor_key = key;
@@ -1295,22 +1440,22 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     if (i0 && ex0 < tK) { i0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
                     if (i1 && ex1 < tK) { i1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
                 }
+                float ev;
                 if (__any_sync(FULL, i0)) {
                     const float xp = warp_max(i0 ? ex0 : NINF);
-                    if (!wq_push<true>(q, xp, r0, lane)) drop_floor(xp);
+                    if (wq_push_evict<true>(q, xp, r0, lane, ev)) drop_floor(ev);
                 }
                 if (__any_sync(FULL, i1)) {
                     const float xp = warp_max(i1 ? ex1 : NINF);
-                    if (!wq_push<true>(q, xp, r1, lane)) drop_floor(xp);
+                    if (wq_push_evict<true>(q, xp, r1, lane, ev)) drop_floor(ev);
                 }
             }
-            const float bound = wq_top<true>(q);
-            while (active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound) replay_front();
+            const float bound = wq_top<true>(q);  // -inf when empty: replay everything pending
+            replay_while([&] { return active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound; });
             active = active && remaining > 0;
-            if (!__any_sync(FULL, active)) break;
+            if (!popped || !__any_sync(FULL, active)) break;
         }
         if (__any_sync(FULL, stop)) break;
-        while (active && remaining > 0 && keys[0] != kEmptyKeyDesc) replay_front();
         if (active && remaining > 0 && floor_key < 0) {
             atomicOr(err, kErrReplayMismatch);
             remaining = 0;
@@ -1340,6 +1485,10 @@ __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int l
 
 template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
+    extern __shared__ float4 s_top[];
+    for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    __syncthreads();
+    const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -1361,13 +1510,13 @@ __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
         float3 o, d;
         camera_ray(cam, px, py, o, d);
         if (MODE == 2)
-            trace_forward_bf<K, COUNT>(A.rec, A.nodes, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count, cnt,
+            trace_forward_bf<K, COUNT>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count, cnt,
                                        A.err);
         else if (MODE == 1)
-            trace_forward_packet<K, COUNT>(A.rec, A.nodes, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+            trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                            cnt, A.err);
         else if (valid)
-            trace_forward<K, COUNT>(A.rec, A.nodes, A.P, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
+            trace_forward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
         if (valid) {
             A.rgb[3 * pix + 0] = fmaf(T, A.P.bg[0], C0);
             A.rgb[3 * pix + 1] = fmaf(T, A.P.bg[1], C1);
@@ -1397,6 +1546,10 @@ __global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
 
 template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
+    extern __shared__ float4 s_top[];
+    for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    __syncthreads();
+    const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -1428,11 +1581,11 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
             if (COUNT) ++rays;
         }
         if (MODE == 2)
-            trace_backward_bf<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward_bf<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         else if (MODE == 1)
-            trace_backward_packet<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         else if (n > 0)
-            trace_backward<K, COUNT>(A.rec, A.nodes, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         if (!PERSIST) break;
     }
     if (COUNT) {
@@ -1546,35 +1699,39 @@ __global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs
 // host launchers
 // ---------------------------------------------------------------------------------------------
 template <int K, bool PERSIST, bool COUNT, int MODE>
-static int occupancy_of(bool backward, int block) {
+static int occupancy_of(bool backward, int block, size_t smem) {
     int nb = 0;
     if (backward)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, COUNT, MODE>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, COUNT, MODE>, block, smem);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, COUNT, MODE>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, COUNT, MODE>, block, smem);
     return nb;
 }
 
 template <int K, bool COUNT>
-static int occupancy_m(bool backward, int block, int mode) {
-    if (mode == 2) return occupancy_of<K, true, COUNT, 2>(backward, block);
-    if (mode == 1) return occupancy_of<K, true, COUNT, 1>(backward, block);
-    return occupancy_of<K, true, COUNT, 0>(backward, block);
+static int occupancy_m(bool backward, int block, int mode, size_t smem) {
+    if (mode == 2) return occupancy_of<K, true, COUNT, 2>(backward, block, smem);
+    if (mode == 1) return occupancy_of<K, true, COUNT, 1>(backward, block, smem);
+    return occupancy_of<K, true, COUNT, 0>(backward, block, smem);
 }
 
-int persistent_grid(bool backward, int K, int block, bool count, int mode, int sms) {
+static size_t smem_bytes(int n_top) { return (size_t)n_top * 4 * sizeof(float4); }
+
+int persistent_grid(bool backward, int K, int block, bool count, int mode, int n_top, int sms) {
+    const size_t sm = smem_bytes(n_top);
     int nb = 1;
-    if (K == 8) nb = count ? occupancy_m<8, true>(backward, block, mode) : occupancy_m<8, false>(backward, block, mode);
+    if (K == 8) nb = count ? occupancy_m<8, true>(backward, block, mode, sm) : occupancy_m<8, false>(backward, block, mode, sm);
     else if (K == 16)
-        nb = count ? occupancy_m<16, true>(backward, block, mode) : occupancy_m<16, false>(backward, block, mode);
-    else nb = count ? occupancy_m<32, true>(backward, block, mode) : occupancy_m<32, false>(backward, block, mode);
+        nb = count ? occupancy_m<16, true>(backward, block, mode, sm) : occupancy_m<16, false>(backward, block, mode, sm);
+    else nb = count ? occupancy_m<32, true>(backward, block, mode, sm) : occupancy_m<32, false>(backward, block, mode, sm);
     return std::max(1, nb) * sms;
 }
 
 template <int K, bool PERSIST, bool COUNT, int MODE>
 static void launch_one(bool backward, const FwdArgs& A, const BwdArgs* B, int grid, int block, cudaStream_t st) {
-    if (backward) k_render_bwd<K, PERSIST, COUNT, MODE><<<grid, block, 0, st>>>(A, *B);
-    else k_render_fwd<K, PERSIST, COUNT, MODE><<<grid, block, 0, st>>>(A);
+    const size_t sm = smem_bytes(A.n_top);
+    if (backward) k_render_bwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A, *B);
+    else k_render_fwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A);
 }
 
 template <int K, bool PERSIST, bool COUNT>

@@ -19,6 +19,7 @@ struct rs_accel {
     // records and boxes in Morton order
     float4* rec = nullptr;   // 4 per Gaussian
     float* pbox = nullptr;   // 6 per Gaussian
+    float4* sph = nullptr;   // 1 per Gaussian: bounding sphere (mean, padded radius^2)
     // sort
     uint64_t* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
@@ -33,6 +34,8 @@ struct rs_accel {
     float* nbox = nullptr;   // 6 per internal node
     int* counter = nullptr;
     float4* nodes = nullptr; // 4 per internal node (>= 1 node)
+    float4* top = nullptr;   // 4 per staged node (kMaxSmemNodes), remapped copies of the top nodes
+    int n_top = 0;           // staged nodes (0: no staging; the root is then node 0)
     int* err = nullptr;      // device error word
 };
 

@@ -22,7 +22,9 @@ namespace rs {
 // ref >= 0 is an internal node; ref < 0 is a leaf holding Gaussians [~ref, ~ref + count).
 // ---------------------------------------------------------------------------------------------
 
-constexpr int kStackSize = 96;         // >= depth of a radix tree over 64-bit codes + 32-bit ids
+constexpr int kStackSize = 96;
+constexpr int kMaxSmemNodes = 512;        // staged top nodes (64 B each) in shared memory
+constexpr int kTopRef = 0x40000000;       // node reference kTopRef + s = staged slot s         // >= depth of a radix tree over 64-bit codes + 32-bit ids
 constexpr int64_t kEmptyKey = INT64_MAX;  // empty slot of an ascending k-buffer
 constexpr int64_t kEmptyKeyDesc = -1;     // empty slot of a descending k-buffer
 

@@ -12,7 +12,10 @@ namespace rs {
 
 struct FwdArgs {
     const float4* rec;
+    const float4* sph;    // bounding spheres (Morton order)
     const float4* nodes;
+    const float4* top;    // staged top nodes (n_top of them; root = kTopRef when n_top > 0)
+    int n_top;
     const DevCam* cams;
     int n_cams;
     int cam_single;       // >= 0: plain launch of this camera only; -1: persistent over all
@@ -36,7 +39,7 @@ struct BwdArgs {
     float4* gtmp;  // 4 per Gaussian (Morton order): (dM row k, dm_k) k = 0..2, (dop, drgb)
 };
 
-int persistent_grid(bool backward, int K, int block, bool count, int mode, int sms);
+int persistent_grid(bool backward, int K, int block, bool count, int mode, int n_top, int sms);
 cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,
                            cudaStream_t st);
 cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,

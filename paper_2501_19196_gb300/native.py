@@ -45,7 +45,7 @@ class RsGaussianGrads(ctypes.Structure):
 
 class RsTuneParams(ctypes.Structure):
     _fields_ = [("tile_w", i32), ("tile_h", i32), ("kbuf", i32), ("leaf_size", i32), ("morton_bits", i32),
-                ("persistent", i32), ("block_warps", i32), ("traversal", i32)]
+                ("persistent", i32), ("block_warps", i32), ("traversal", i32), ("smem_nodes", i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

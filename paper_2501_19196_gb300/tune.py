@@ -28,7 +28,7 @@ def candidates(tiles=((8, 4), (4, 8)), kbufs=(8, 16, 32), leaves=(1, 2, 4), warp
     """The cross product of the given tunables (all persistent launches by default)."""
     out = []
     for (tw, th), k, leaf, w, mb, tr in itertools.product(tiles, kbufs, leaves, warps, morton, traversal):
-        out.append(native.RsTuneParams(tw, th, k, leaf, mb, persistent, w, tr))
+        out.append(native.RsTuneParams(tw, th, k, leaf, mb, persistent, w, tr, 256))
     return out
 
 

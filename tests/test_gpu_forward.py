@@ -228,6 +228,8 @@ def test_tunables_and_launch_modes_bit_identical():
                dict(tile_w=4), dict(tile_w=16), dict(tile_w=32), dict(persistent=0), dict(morton_bits=10),
                dict(morton_bits=20), dict(traversal=0), dict(traversal=0, leaf_size=1, kbuf=8),
                dict(traversal=2), dict(traversal=2, leaf_size=1, kbuf=8), dict(traversal=2, persistent=0),
+               dict(smem_nodes=0), dict(smem_nodes=512), dict(smem_nodes=1, traversal=2),
+               dict(smem_nodes=3, traversal=0),
                dict(block_warps=1), dict(block_warps=2)):
         out = gpu_render(sc, cams, prm, tune=native.default_tune(**kw))
         for k in ("rgb", "alpha", "depth"):
