@@ -229,6 +229,30 @@ rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int
                   const rs_frame_grad* dl, rs_gaussian_grads* scratch_grads,
                   rs_tune_params* best, float* ms_out, void* cuda_stream);
 
+/* ---- Fixed-scratch render (no counterpart in the paper) ----------------------------------
+ * For callers that cannot allocate device memory -- code that runs while a CUDA graph is being
+ * captured under a no-allocation policy, plug-ins whose host application owns every device
+ * allocation, tools that must not grow the process's memory -- this entry point builds the
+ * acceleration structure and renders the cameras (the work of rs_build_accel + rs_render)
+ * without any cudaMalloc, cudaFree or other allocating call.  Every intermediate lives in one
+ * file-scope device array of fixed size (about 13 MB, held by every GPU that loads the
+ * library until the process exits).  The caller still passes the scene, the cameras and the
+ * output buffers; there is no per-ray state for a backward pass.
+ *   - Limits: g->n <= RS_FIXED_MAX_GAUSSIANS, n_cams <= RS_FIXED_MAX_CAMERAS, sum of W*H <=
+ *     RS_FIXED_MAX_PIXELS; larger requests return RS_ERR_INVALID_ARG before any launch.
+ *   - The first call on a device resolves the array's device address (set-up, once per
+ *     device, with that device current); make it before any stream capture.
+ *   - All calls share the array and it keeps the previous call's contents (the call clears
+ *     what must start at zero): calls that overlap on the GPU race with each other.
+ *   - Q plays the role of rs_build_accel's Q_box.  Device consistency checks are not reported
+ *     (there is no handle to query). */
+#define RS_FIXED_MAX_GAUSSIANS 32768
+#define RS_FIXED_MAX_PIXELS 262144
+#define RS_FIXED_MAX_CAMERAS 16
+rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_camera* cams, int32_t n_cams,
+                                  const rs_render_params* params, const rs_tune_params* tune,
+                                  rs_frame* out, void* cuda_stream);
+
 /* Free a handle (NULL is accepted).  Synchronises the device before freeing. */
 rs_status rs_accel_destroy(rs_accel* accel);
 rs_status rs_state_destroy(rs_fwd_state* state);

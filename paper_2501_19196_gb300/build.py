@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libraysplats.so"
-SOURCES = ["lbvh.cu", "render.cu", "api.cu"]
+SOURCES = ["lbvh.cu", "render.cu", "api.cu", "fixed_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

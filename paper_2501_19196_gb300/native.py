@@ -64,6 +64,7 @@ _SIGS = {
     "rs_render_backward": (i32, [P, P, P, P, P, P, P]),
     "rs_render_backward_counted": (i32, [P, P, P, P, P, P, P, P]),
     "rs_tune": (i32, [P, f32, P, i32, P, P, i32, i32, P, P, P, P, P, P]),
+    "rs_render_fixed_scratch": (i32, [P, P, i32, P, P, P, P]),
     "rs_accel_destroy": (i32, [P]),
     "rs_state_destroy": (i32, [P]),
     "rs_check_device": (i32, [P, P, P]),
