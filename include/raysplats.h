@@ -235,7 +235,7 @@ rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int
  * allocation, tools that must not grow the process's memory -- this entry point builds the
  * acceleration structure and renders the cameras (the work of rs_build_accel + rs_render)
  * without any cudaMalloc, cudaFree or other allocating call.  Every intermediate lives in one
- * file-scope device array of fixed size (about 13 MB, held by every GPU that loads the
+ * file-scope device array of fixed size (about 12 MB, held by every GPU that loads the
  * library until the process exits).  The caller still passes the scene, the cameras and the
  * output buffers; there is no per-ray state for a backward pass.
  *   - Limits: g->n <= RS_FIXED_MAX_GAUSSIANS, n_cams <= RS_FIXED_MAX_CAMERAS, sum of W*H <=

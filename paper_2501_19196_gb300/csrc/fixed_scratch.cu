@@ -8,7 +8,7 @@
 // file-scope __device__ array of fixed size, shared by all calls on a device.
 //
 // Limits: n <= RS_FIXED_MAX_GAUSSIANS, sum of W*H <= RS_FIXED_MAX_PIXELS, n_cams <=
-// RS_FIXED_MAX_CAMERAS; the array is about 13 MB and every GPU that loads the library holds
+// RS_FIXED_MAX_CAMERAS; the array is about 12 MB and every GPU that loads the library holds
 // it until the process exits.  The first call on a device resolves the array's device address
 // (cudaGetSymbolAddress with that device current); make that first call before any stream
 // capture.  Calls share the array and keep the previous call's contents, so calls that overlap
