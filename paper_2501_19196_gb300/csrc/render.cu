@@ -962,16 +962,32 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
 // ---------------------------------------------------------------------------------------------
 constexpr int kQSlots = 4;
 
+// Each occupied slot holds one 32-bit key: the priority's FP32 bit pattern with its 7 low
+// mantissa bits replaced by the slot's warp-wide id (lane * kQSlots + slot).  Priorities are
+// >= 0, so the keys order as unsigned integers and one redux.sync finds the extreme slot.
+// Forward (min-queue) priorities are rounded down and adjoint (max-queue) priorities up by at
+// most 127 ulps: both only make the finalisation bounds more conservative.
 struct WarpQueue {
-    float pr[kQSlots];  // priority (+inf = empty for the min-queue, -inf for the max-queue)
+    uint32_t key[kQSlots];
     int nd[kQSlots];
 };
+
+template <bool MAXQ>
+__device__ __forceinline__ uint32_t wq_empty() {
+    return MAXQ ? 0u : 0xffffffffu;
+}
+
+template <bool MAXQ>
+__device__ __forceinline__ uint32_t wq_bits(float pr) {
+    if (MAXQ) return (__float_as_uint(fmaxf(pr, 1.17549435e-38f)) + 0x7fu) & ~0x7fu;  // round up, > 0
+    return __float_as_uint(fmaxf(pr, 0.f)) & ~0x7fu;                                   // round down
+}
 
 template <bool MAXQ>
 __device__ __forceinline__ void wq_init(WarpQueue& q) {
 #pragma unroll
     for (int s = 0; s < kQSlots; ++s) {
-        q.pr[s] = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+        q.key[s] = wq_empty<MAXQ>();
         q.nd[s] = 0;
     }
 }
@@ -979,13 +995,14 @@ __device__ __forceinline__ void wq_init(WarpQueue& q) {
 // push a (uniform) entry; false when the queue is full
 template <bool MAXQ>
 __device__ __forceinline__ bool wq_push(WarpQueue& q, float pr, int node, int lane) {
-    const float empty = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    const uint32_t bits = wq_bits<MAXQ>(pr);
 #pragma unroll
     for (int s = 0; s < kQSlots; ++s) {
-        const unsigned m = __ballot_sync(0xffffffffu, q.pr[s] == empty);
+        const unsigned m = __ballot_sync(0xffffffffu, q.key[s] == wq_empty<MAXQ>());
         if (m) {
-            if (lane == __ffs(m) - 1) {
-                q.pr[s] = pr;
+            const int owner = __ffs(m) - 1;
+            if (lane == owner) {
+                q.key[s] = bits | (uint32_t)(owner * kQSlots + s);
                 q.nd[s] = node;
             }
             return true;
@@ -994,116 +1011,80 @@ __device__ __forceinline__ bool wq_push(WarpQueue& q, float pr, int node, int la
     return false;
 }
 
-// push with eviction: when the queue is full, the worst entry among the queue and the new one
-// (largest priority for the min-queue, smallest for the max-queue) is dropped; returns true and
-// its priority in *evicted when something was dropped.
 template <bool MAXQ>
-__device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, int lane, float& evicted) {
-    if (wq_push<MAXQ>(q, pr, node, lane)) return false;
-    // worst slot of the (full) queue
-    float v = q.pr[0];
-    int bs = 0;
+__device__ __forceinline__ uint32_t wq_extreme_key(const WarpQueue& q) {
+    uint32_t v = q.key[0];
 #pragma unroll
-    for (int s = 1; s < kQSlots; ++s) {
-        const bool worse = MAXQ ? (q.pr[s] < v) : (q.pr[s] > v);
-        if (worse) {
-            v = q.pr[s];
-            bs = s;
-        }
-    }
-    int id = lane * kQSlots + bs;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
-        const int oid = __shfl_xor_sync(0xffffffffu, id, off);
-        const bool worse = MAXQ ? (ov < v || (ov == v && oid < id)) : (ov > v || (ov == v && oid < id));
-        if (worse) {
-            v = ov;
-            id = oid;
-        }
-    }
-    const bool replace = MAXQ ? (v < pr) : (v > pr);
-    if (!replace) {
-        evicted = pr;  // the new entry is the worst: drop it
-        return true;
-    }
-    const int owner = id / kQSlots, slot = id % kQSlots;
-    if (lane == owner) {
-#pragma unroll
-        for (int s = 0; s < kQSlots; ++s)
-            if (slot == s) {
-                q.pr[s] = pr;
-                q.nd[s] = node;
-            }
-    }
-    evicted = v;
-    return true;
+    for (int s = 1; s < kQSlots; ++s) v = MAXQ ? max(v, q.key[s]) : min(v, q.key[s]);
+    return MAXQ ? __reduce_max_sync(0xffffffffu, v) : __reduce_min_sync(0xffffffffu, v);
 }
 
-// extreme priority over the whole queue (uniform); empty value when the queue is empty
+// extreme priority over the whole queue (uniform); +inf (min-queue) / -inf (max-queue) if empty
 template <bool MAXQ>
 __device__ __forceinline__ float wq_top(const WarpQueue& q) {
-    float v = q.pr[0];
-#pragma unroll
-    for (int s = 1; s < kQSlots; ++s) v = MAXQ ? fmaxf(v, q.pr[s]) : fminf(v, q.pr[s]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float o = __shfl_xor_sync(0xffffffffu, v, off);
-        v = MAXQ ? fmaxf(v, o) : fminf(v, o);
-    }
-    return v;
+    const uint32_t v = wq_extreme_key<MAXQ>(q);
+    if (v == wq_empty<MAXQ>()) return MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    return __uint_as_float(v & ~0x7fu);
 }
 
-// pop the extreme entry (ties: lowest slot id); returns false when empty
+// pop the extreme entry; returns false when empty
 template <bool MAXQ>
 __device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int lane) {
-    const float empty = MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
-    float v = q.pr[0];
-    int bs = 0;
-#pragma unroll
-    for (int s = 1; s < kQSlots; ++s) {
-        const bool better = MAXQ ? (q.pr[s] > v) : (q.pr[s] < v);
-        if (better) {
-            v = q.pr[s];
-            bs = s;
-        }
-    }
-    int id = lane * kQSlots + bs;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, off);
-        const int oid = __shfl_xor_sync(0xffffffffu, id, off);
-        const bool better = MAXQ ? (ov > v || (ov == v && oid < id)) : (ov < v || (ov == v && oid < id));
-        if (better) {
-            v = ov;
-            id = oid;
-        }
-    }
-    if (v == empty) return false;
-    const int owner = id / kQSlots, slot = id % kQSlots;
+    const uint32_t v = wq_extreme_key<MAXQ>(q);
+    if (v == wq_empty<MAXQ>()) return false;
+    const int gid = (int)(v & 0x7fu);
+    const int owner = gid / kQSlots, slot = gid % kQSlots;
     int mine = q.nd[0];
 #pragma unroll
     for (int s = 1; s < kQSlots; ++s)
         if (slot == s) mine = q.nd[s];
     node = __shfl_sync(0xffffffffu, mine, owner);
-    pr = v;
+    pr = __uint_as_float(v & ~0x7fu);
     if (lane == owner) {
 #pragma unroll
         for (int s = 0; s < kQSlots; ++s)
-            if (slot == s) q.pr[s] = empty;
+            if (slot == s) q.key[s] = wq_empty<MAXQ>();
     }
     return true;
 }
 
-__device__ __forceinline__ float warp_min(float v) {
+// push with eviction: when the queue is full, the worst entry among the queue and the new one
+// (largest priority for the min-queue, smallest for the max-queue) is dropped; returns true and
+// its (rounded, conservative) priority in *evicted when something was dropped.
+template <bool MAXQ>
+__device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, int lane, float& evicted) {
+    if (wq_push<MAXQ>(q, pr, node, lane)) return false;
+    uint32_t v = q.key[0];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
+    for (int s = 1; s < kQSlots; ++s) v = MAXQ ? min(v, q.key[s]) : max(v, q.key[s]);
+    v = MAXQ ? __reduce_min_sync(0xffffffffu, v) : __reduce_max_sync(0xffffffffu, v);  // worst key
+    const uint32_t nb = wq_bits<MAXQ>(pr);
+    const uint32_t wb = v & ~0x7fu;
+    const bool replace = MAXQ ? (wb < nb) : (wb > nb);
+    if (!replace) {
+        evicted = __uint_as_float(nb);
+        return true;
+    }
+    const int gid = (int)(v & 0x7fu);
+    const int owner = gid / kQSlots, slot = gid % kQSlots;
+    if (lane == owner) {
+#pragma unroll
+        for (int s = 0; s < kQSlots; ++s)
+            if (slot == s) {
+                q.key[s] = nb | (uint32_t)gid;
+                q.nd[s] = node;
+            }
+    }
+    evicted = __uint_as_float(wb);
+    return true;
 }
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
-    return v;
+
+// warp-wide min / max of non-negative floats (their bit patterns order as unsigned integers)
+__device__ __forceinline__ float warp_min_nonneg(float v) {
+    return __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(v)));
+}
+__device__ __forceinline__ float warp_max_nonneg(float v) {
+    return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
 }
 
 template <int K, bool COUNT>
@@ -1253,11 +1234,11 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                 }
                 float ev;
                 if (__any_sync(FULL, i0)) {
-                    const float ep = warp_min(i0 ? e0 : INF);
+                    const float ep = warp_min_nonneg(i0 ? e0 : INF);  // e0 >= tlo >= 0
                     if (wq_push_evict<false>(q, ep, r0, lane, ev)) drop_cap(ev);
                 }
                 if (__any_sync(FULL, i1)) {
-                    const float ep = warp_min(i1 ? e1 : INF);
+                    const float ep = warp_min_nonneg(i1 ? e1 : INF);
                     if (wq_push_evict<false>(q, ep, r1, lane, ev)) drop_cap(ev);
                 }
             }
@@ -1442,11 +1423,11 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 }
                 float ev;
                 if (__any_sync(FULL, i0)) {
-                    const float xp = warp_max(i0 ? ex0 : NINF);
+                    const float xp = warp_max_nonneg(i0 ? ex0 : 0.f);  // ex0 >= tfl >= 0
                     if (wq_push_evict<true>(q, xp, r0, lane, ev)) drop_floor(ev);
                 }
                 if (__any_sync(FULL, i1)) {
-                    const float xp = warp_max(i1 ? ex1 : NINF);
+                    const float xp = warp_max_nonneg(i1 ? ex1 : 0.f);
                     if (wq_push_evict<true>(q, xp, r1, lane, ev)) drop_floor(ev);
                 }
             }
@@ -1484,7 +1465,7 @@ __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int l
 }
 
 template <int K, bool PERSIST, bool COUNT, int MODE>
-__global__ void __launch_bounds__(128) k_render_fwd(FwdArgs A) {
+__global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
     extern __shared__ float4 s_top[];
     for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
