@@ -134,7 +134,8 @@ typedef struct {
  *   traversal       0: each lane traverses its own ray (depth first); 1: the 32 rays of a
  *                   tile traverse as a warp packet (shared node sequence, per-ray state, depth
  *                   first); 2: warp packet in best-first order of box entry (a priority queue
- *                   distributed over the warp's registers)
+ *                   distributed over the warp's registers); 3: as 2 over 4-wide nodes (each
+ *                   binary node's grandchildren; rs_build_accel builds them when given 3)
  *   smem_nodes      0..512: the top BVH nodes (breadth first) that rs_build_accel stages for
  *                   the render kernels' shared memory (64 B each); 0 disables staging */
 typedef struct {
@@ -168,7 +169,7 @@ int32_t rs_abi_version(void);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rs_last_error(void);
 
-/* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 8, 63-bit codes,
+/* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 16, 63-bit codes,
  * persistent launch, 4 warps per CTA, best-first warp-packet traversal, 256 staged nodes). */
 rs_status rs_default_tune(rs_tune_params* out);
 

@@ -66,9 +66,9 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
         return set_error(RS_ERR_INVALID_ARG, "block_warps %d: must be 1..4", t->block_warps);
     if (t->smem_nodes < 0 || t->smem_nodes > kMaxSmemNodes)
         return set_error(RS_ERR_INVALID_ARG, "smem_nodes %d: must be 0..%d", t->smem_nodes, kMaxSmemNodes);
-    if (t->traversal < 0 || t->traversal > 2)
-        return set_error(RS_ERR_INVALID_ARG, "traversal %d: must be 0 (per ray), 1 (warp packet) or 2 (best-first "
-                         "warp packet)", t->traversal);
+    if (t->traversal < 0 || t->traversal > 3)
+        return set_error(RS_ERR_INVALID_ARG, "traversal %d: must be 0 (per ray), 1 (warp packet), 2 (best-first "
+                         "warp packet) or 3 (best-first warp packet over 4-wide nodes)", t->traversal);
     return RS_OK;
 }
 
@@ -98,7 +98,7 @@ rs_status rs_default_tune(rs_tune_params* out) {
     out->tile_w = 8;
     out->tile_h = 4;
     out->kbuf = 32;
-    out->leaf_size = 8;
+    out->leaf_size = 16;
     out->morton_bits = 21;
     out->persistent = 1;
     out->block_warps = 4;
@@ -143,6 +143,14 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
         }
         A->cap = cap;
     }
+    if (tune->traversal == 3 && (!A->wide || A->wide_cap < n)) {
+        if ((st = dmalloc(A->wide, 8 * std::max<int64_t>(1, n)))) {
+            A->wide_cap = 0;
+            return st;
+        }
+        A->wide_cap = n;
+    }
+    A->has_wide = tune->traversal == 3;
     A->n = n;
     A->leaf_size = tune->leaf_size;
     A->morton_bits = tune->morton_bits;
@@ -158,6 +166,8 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     if (st) return st;
     if ((st = check_tune(tune, false))) return st;
     if (!accel || accel->n != g->n) return set_error(RS_ERR_INVALID_ARG, "accel is NULL or built for another n");
+    if (tune->traversal == 3 && !accel->has_wide)
+        return set_error(RS_ERR_INVALID_ARG, "traversal 3 needs an accel built with traversal 3 (4-wide nodes)");
     if (!cams || n_cams < 1) return set_error(RS_ERR_INVALID_ARG, "need at least one camera");
     if (!p) return set_error(RS_ERR_INVALID_ARG, "render params are NULL");
     if (!(p->Q > 0.f) || !(p->Q <= accel->Q_box))
@@ -272,6 +282,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     A.nodes = accel->nodes;
     A.top = accel->top;
     A.n_top = accel->n_top;
+    A.wide = accel->wide;
     A.cams = S->cams_dev;
     A.n_cams = n_cams;
     A.tile_w = tw;
@@ -332,6 +343,8 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
     if (!state || state->n_pix <= 0) return set_error(RS_ERR_INVALID_ARG, "state is NULL or holds no render");
     if (!accel || accel != state->accel || accel->n != g->n || state->n_gauss != g->n)
         return set_error(RS_ERR_INVALID_ARG, "accel / scene differ from the forward pass");
+    if (tune->traversal == 3 && !accel->has_wide)
+        return set_error(RS_ERR_INVALID_ARG, "traversal 3 needs an accel built with traversal 3 (4-wide nodes)");
     if (tune->tile_w != state->tile_w)
         return set_error(RS_ERR_INVALID_ARG, "tile shape differs from the forward pass");
     if (!dl || !dl->d_rgb) return set_error(RS_ERR_INVALID_ARG, "upstream gradient d_rgb is NULL");
@@ -353,6 +366,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
     A.nodes = accel->nodes;
     A.top = accel->top;
     A.n_top = accel->n_top;
+    A.wide = accel->wide;
     A.cams = S->cams_dev;
     A.n_cams = S->n_cams;
     A.tile_w = S->tile_w;
@@ -411,7 +425,7 @@ rs_status rs_accel_destroy(rs_accel* A) {
     cudaDeviceSynchronize();
     void* ptrs[] = {A->rec,  A->pbox,  A->sph, A->keys[0], A->keys[1], A->vals[0], A->vals[1], A->hist,   A->bounds,
                     A->left, A->right, A->first,   A->last,    A->parent,  A->nbox,    A->counter, A->nodes,
-                    A->top,  A->err};
+                    A->top,  A->wide, A->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete A;

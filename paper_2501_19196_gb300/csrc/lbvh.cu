@@ -455,6 +455,60 @@ __global__ void __launch_bounds__(kMaxSmemNodes) k_stage_top(const float4* __res
     }
 }
 
+// 4-wide nodes: for every emitted binary node p, its children are p's grandchildren (a leaf
+// child stays a child).  Descending into an internal grandchild g then uses g's own wide node,
+// so a traversal of the wide nodes visits every other level of the binary tree.  Layout per
+// node (8 float4): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of the four children, refs, counts;
+// unused slots have ref kEmptyRef.  Only emitted nodes (size > leaf_size, or the root) are
+// read: their child references are valid by construction.
+__global__ void k_wide(const float4* __restrict__ nodes, const int* __restrict__ first, const int* __restrict__ last,
+                       int64_t n_int, int leaf_size, float4* __restrict__ wide) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n_int) return;
+    if (first && p != 0 && (last[p] - first[p] + 1) <= leaf_size) return;  // not emitted (n == 1: first is NULL)
+    float lo[3][4], hi[3][4];
+    int ref[4], cnt[4];
+    int m = 0;
+    auto add = [&](const float4 a, const float4 b, const float4 z, int side, int r, int c) {
+        // box of child `side` of a binary node (a = side 0 xy, b = side 1 xy, z = both z)
+        const float4 xy = side ? b : a;
+        lo[0][m] = xy.x; hi[0][m] = xy.y; lo[1][m] = xy.z; hi[1][m] = xy.w;
+        lo[2][m] = side ? z.z : z.x; hi[2][m] = side ? z.w : z.y;
+        ref[m] = r;
+        cnt[m] = c;
+        ++m;
+    };
+    const float4 n0 = nodes[4 * p], n1 = nodes[4 * p + 1], n2 = nodes[4 * p + 2], n3 = nodes[4 * p + 3];
+    const int r[2] = {__float_as_int(n3.x), __float_as_int(n3.y)};
+    const int c[2] = {__float_as_int(n3.z), __float_as_int(n3.w)};
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if (r[side] >= 0) {
+            const int g = r[side];
+            const float4 g0 = nodes[4 * g], g1 = nodes[4 * g + 1], g2 = nodes[4 * g + 2], g3 = nodes[4 * g + 3];
+            add(g0, g1, g2, 0, __float_as_int(g3.x), __float_as_int(g3.z));
+            add(g0, g1, g2, 1, __float_as_int(g3.y), __float_as_int(g3.w));
+        } else {
+            add(n0, n1, n2, side, r[side], c[side]);
+        }
+    }
+    for (; m < 4; ++m) {
+        lo[0][m] = lo[1][m] = lo[2][m] = 3.0e38f;
+        hi[0][m] = hi[1][m] = hi[2][m] = -3.0e38f;
+        ref[m] = kEmptyRef;
+        cnt[m] = 0;
+    }
+    float4* w = wide + 8 * p;
+    w[0] = make_float4(lo[0][0], lo[0][1], lo[0][2], lo[0][3]);
+    w[1] = make_float4(hi[0][0], hi[0][1], hi[0][2], hi[0][3]);
+    w[2] = make_float4(lo[1][0], lo[1][1], lo[1][2], lo[1][3]);
+    w[3] = make_float4(hi[1][0], hi[1][1], hi[1][2], hi[1][3]);
+    w[4] = make_float4(lo[2][0], lo[2][1], lo[2][2], lo[2][3]);
+    w[5] = make_float4(hi[2][0], hi[2][1], hi[2][2], hi[2][3]);
+    w[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
+    w[7] = make_float4(__int_as_float(cnt[0]), __int_as_float(cnt[1]), __int_as_float(cnt[2]), __int_as_float(cnt[3]));
+}
+
 // single Gaussian: a root whose first child is the leaf and whose second child is empty
 __global__ void k_single_root(const float* __restrict__ pbox, float4* __restrict__ nodes) {
     const float* b = pbox;
@@ -502,6 +556,11 @@ rs_status build_accel_device(Accel& A, const rs_gaussians& g, const rs_tune_para
     A.n_top = (int)std::min<int64_t>(std::min(tp.smem_nodes, kMaxSmemNodes), std::max<int64_t>(1, n - 1));
     if (tp.smem_nodes <= 0) A.n_top = 0;
     if (A.n_top > 0) k_stage_top<<<1, kMaxSmemNodes, 0, st>>>(A.nodes, A.n_top, A.top);
+    if (A.has_wide) {
+        const int64_t n_int = std::max<int64_t>(1, n - 1);
+        k_wide<<<grid_for(n_int, 256), 256, 0, st>>>(A.nodes, n == 1 ? nullptr : A.first, n == 1 ? nullptr : A.last,
+                                                    n_int, tp.leaf_size, A.wide);
+    }
     return cuda_check("rs_build_accel launch");
 }
 

@@ -49,6 +49,15 @@ struct NodeSrc {
     const float4* __restrict__ g;
     const float4* s;
     int root;
+    const float4* __restrict__ w;  // 4-wide nodes (8 float4 each), indexed like the binary nodes
+};
+
+// The children of one node as seen by the traversal: W = 2 reads a binary node (possibly staged
+// in shared memory), W = 4 a wide node (the node's grandchildren; empty slots have ref kEmptyRef).
+template <int W>
+struct Children {
+    float lo[3][W], hi[3][W];
+    int ref[W], cnt[W];
 };
 
 __device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& n0, float4& n1, float4& n2,
@@ -65,6 +74,51 @@ __device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& 
         n2 = __ldg(ns.g + 4 * node + 2);
         n3 = __ldg(ns.g + 4 * node + 3);
     }
+}
+
+template <int W>
+__device__ __forceinline__ void fetch_children(const NodeSrc& ns, int node, Children<W>& ch);
+
+template <>
+__device__ __forceinline__ void fetch_children<2>(const NodeSrc& ns, int node, Children<2>& ch) {
+    float4 n0, n1, n2, n3;
+    fetch_node(ns, node, n0, n1, n2, n3);
+    ch.lo[0][0] = n0.x; ch.hi[0][0] = n0.y; ch.lo[1][0] = n0.z; ch.hi[1][0] = n0.w;
+    ch.lo[0][1] = n1.x; ch.hi[0][1] = n1.y; ch.lo[1][1] = n1.z; ch.hi[1][1] = n1.w;
+    ch.lo[2][0] = n2.x; ch.hi[2][0] = n2.y; ch.lo[2][1] = n2.z; ch.hi[2][1] = n2.w;
+    ch.ref[0] = __float_as_int(n3.x); ch.ref[1] = __float_as_int(n3.y);
+    ch.cnt[0] = __float_as_int(n3.z); ch.cnt[1] = __float_as_int(n3.w);
+}
+
+template <>
+__device__ __forceinline__ void fetch_children<4>(const NodeSrc& ns, int node, Children<4>& ch) {
+    const float4* p = ns.w + 8 * node;
+    const float4 lx = __ldg(p + 0), hx = __ldg(p + 1), ly = __ldg(p + 2), hy = __ldg(p + 3);
+    const float4 lz = __ldg(p + 4), hz = __ldg(p + 5), rf = __ldg(p + 6), ct = __ldg(p + 7);
+    const float a[8][4] = {{lx.x, lx.y, lx.z, lx.w}, {hx.x, hx.y, hx.z, hx.w}, {ly.x, ly.y, ly.z, ly.w},
+                           {hy.x, hy.y, hy.z, hy.w}, {lz.x, lz.y, lz.z, lz.w}, {hz.x, hz.y, hz.z, hz.w},
+                           {rf.x, rf.y, rf.z, rf.w}, {ct.x, ct.y, ct.z, ct.w}};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        ch.lo[0][c] = a[0][c]; ch.hi[0][c] = a[1][c];
+        ch.lo[1][c] = a[2][c]; ch.hi[1][c] = a[3][c];
+        ch.lo[2][c] = a[4][c]; ch.hi[2][c] = a[5][c];
+        ch.ref[c] = __float_as_int(a[6][c]);
+        ch.cnt[c] = __float_as_int(a[7][c]);
+    }
+}
+
+// entry / exit of child c's box, widened by 1e-6 relative (as slab2)
+template <int W>
+__device__ __forceinline__ void slab_child(const Children<W>& ch, int c, const float3 o, const float3 inv, float& en,
+                                           float& ex) {
+    const float a0 = (ch.lo[0][c] - o.x) * inv.x, b0 = (ch.hi[0][c] - o.x) * inv.x;
+    const float a1 = (ch.lo[1][c] - o.y) * inv.y, b1 = (ch.hi[1][c] - o.y) * inv.y;
+    const float a2 = (ch.lo[2][c] - o.z) * inv.z, b2 = (ch.hi[2][c] - o.z) * inv.z;
+    const float e = fmaxf(fmaxf(fminf(a0, b0), fminf(a1, b1)), fminf(a2, b2));
+    const float x = fminf(fminf(fmaxf(a0, b0), fmaxf(a1, b1)), fmaxf(a2, b2));
+    en = fmaf(-1e-6f, fabsf(e), e);
+    ex = fmaf(1e-6f, fabsf(x), x);
 }
 
 // Entry and exit parameters of both children's boxes, widened by 1e-6 relative so that rounding
@@ -1087,7 +1141,7 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
     return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
 }
 
-template <int K, bool COUNT>
+template <int K, bool COUNT, int W>
 __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                  const TraceParams& P, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
@@ -1174,40 +1228,47 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     done = true;
                     break;
                 }
-                float4 n0, n1, n2, n3;
-                fetch_node(nodes, node, n0, n1, n2, n3);
+                Children<W> ch;
+                fetch_children<W>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
-                float en0, ex0, en1, ex1;
-                slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
-                const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-                const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
-                const float e0 = fmaxf(en0, tlo), e1 = fmaxf(en1, tlo);
-                bool h0 = false, h1 = false;
+                float e[W], x[W];
+                bool h[W];
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    float en;
+                    slab_child<W>(ch, c, o, inv, en, x[c]);
+                    e[c] = fmaxf(en, tlo);
+                    h[c] = false;
+                }
                 if (need) {
                     const float tcap = cap == kEmptyKey ? INF : key_t(cap);
                     const bool full = keys[K - 1] != kEmptyKey;
                     const float tK = full ? key_t(keys[K - 1]) : INF;
-                    h0 = e0 <= fminf(ex0, tcap);
-                    h1 = e1 <= fminf(ex1, tcap);
-                    if (h0 && e0 > tK) { h0 = false; cap = min(cap, pack_key(e0, 0)); }
-                    if (h1 && e1 > tK) { h1 = false; cap = min(cap, pack_key(e1, 0)); }
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        h[c] = ch.ref[c] != kEmptyRef && e[c] <= fminf(x[c], tcap);
+                        if (h[c] && e[c] > tK) {
+                            h[c] = false;
+                            cap = min(cap, pack_key(e[c], 0));
+                        }
+                    }
                 }
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int rr = side ? r1 : r0;
-                    const bool want = (side ? h1 : h0) && rr < 0;
+                for (int c = 0; c < W; ++c) {
+                    const int rr = ch.ref[c];
+                    const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
-                        const int start = ~rr, num = side ? c1 : c0;
+                        const int start = ~rr, num = ch.cnt[c];
                         for (int qq = start; qq < start + num; ++qq) {
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
-                                Hit h;
-                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                                Hit hh;
+                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
                                 if (COUNT) cnt.tests++;
-                                if (h.hit) {
-                                    const int64_t key = pack_key(h.t1, qq);
+                                if (hh.hit) {
+                                    const int64_t key = pack_key(hh.t1, qq);
                                     if (key > lo_key && key < cap) {
                                         if (key < keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
@@ -1222,24 +1283,29 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                         }
                     }
                 }
-                bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+                bool in[W];
+#pragma unroll
+                for (int c = 0; c < W; ++c) in[c] = h[c] && ch.ref[c] >= 0;
                 if (need) {
                     const float tcap = cap == kEmptyKey ? INF : key_t(cap);
                     const bool full = keys[K - 1] != kEmptyKey;
                     const float tK = full ? key_t(keys[K - 1]) : INF;
-                    if (i0 && e0 > tcap) i0 = false;
-                    if (i1 && e1 > tcap) i1 = false;
-                    if (i0 && e0 > tK) { i0 = false; cap = min(cap, pack_key(e0, 0)); }
-                    if (i1 && e1 > tK) { i1 = false; cap = min(cap, pack_key(e1, 0)); }
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        if (in[c] && e[c] > tcap) in[c] = false;
+                        if (in[c] && e[c] > tK) {
+                            in[c] = false;
+                            cap = min(cap, pack_key(e[c], 0));
+                        }
+                    }
                 }
                 float ev;
-                if (__any_sync(FULL, i0)) {
-                    const float ep = warp_min_nonneg(i0 ? e0 : INF);  // e0 >= tlo >= 0
-                    if (wq_push_evict<false>(q, ep, r0, lane, ev)) drop_cap(ev);
-                }
-                if (__any_sync(FULL, i1)) {
-                    const float ep = warp_min_nonneg(i1 ? e1 : INF);
-                    if (wq_push_evict<false>(q, ep, r1, lane, ev)) drop_cap(ev);
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    if (__any_sync(FULL, in[c])) {
+                        const float ep = warp_min_nonneg(in[c] ? e[c] : INF);  // e >= tlo >= 0
+                        if (wq_push_evict<false>(q, ep, ch.ref[c], lane, ev)) drop_cap(ev);
+                    }
                 }
             }
             const float bound = wq_top<false>(q);  // +inf when empty: composite everything pending
@@ -1254,7 +1320,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     }
 }
 
-template <int K, bool COUNT>
+template <int K, bool COUNT, int W>
 __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                   const TraceParams& P, const float3 o, const float3 d,
                                                   float T_final, int64_t last_key, int n_hits, const float gC[3],
@@ -1364,39 +1430,45 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     stop = true;
                     break;
                 }
-                float4 n0, n1, n2, n3;
-                fetch_node(nodes, node, n0, n1, n2, n3);
+                Children<W> ch;
+                fetch_children<W>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
-                float en0, ex0, en1, ex1;
-                slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
-                const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-                const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
-                bool h0 = false, h1 = false;
+                float en[W], x[W];
+                bool h[W];
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    slab_child<W>(ch, c, o, inv, en[c], x[c]);
+                    h[c] = false;
+                }
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                     const bool full = keys[K - 1] != kEmptyKeyDesc;
                     const float tK = full ? key_t(keys[K - 1]) : NINF;
-                    h0 = en0 <= thi && ex0 >= tfl && ex0 >= en0;
-                    h1 = en1 <= thi && ex1 >= tfl && ex1 >= en1;
-                    if (h0 && ex0 < tK) { h0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
-                    if (h1 && ex1 < tK) { h1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        h[c] = ch.ref[c] != kEmptyRef && en[c] <= thi && x[c] >= tfl && x[c] >= en[c];
+                        if (h[c] && x[c] < tK) {
+                            h[c] = false;
+                            floor_key = max(floor_key, pack_key(x[c], kFloorJ));
+                        }
+                    }
                 }
 #pragma unroll
-                for (int side = 0; side < 2; ++side) {
-                    const int rr = side ? r1 : r0;
-                    const bool want = (side ? h1 : h0) && rr < 0;
+                for (int c = 0; c < W; ++c) {
+                    const int rr = ch.ref[c];
+                    const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
-                        const int start = ~rr, num = side ? c1 : c0;
+                        const int start = ~rr, num = ch.cnt[c];
                         for (int qq = start; qq < start + num; ++qq) {
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
-                                Hit h;
-                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+                                Hit hh;
+                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
                                 if (COUNT) cnt.tests++;
-                                if (h.hit) {
-                                    const int64_t key = pack_key(h.t1, qq);
+                                if (hh.hit) {
+                                    const int64_t key = pack_key(hh.t1, qq);
                                     if (key < hi_key && key > floor_key) {
                                         if (key > keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
@@ -1411,24 +1483,29 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                         }
                     }
                 }
-                bool i0 = h0 && r0 >= 0, i1 = h1 && r1 >= 0;
+                bool in[W];
+#pragma unroll
+                for (int c = 0; c < W; ++c) in[c] = h[c] && ch.ref[c] >= 0;
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                     const bool full = keys[K - 1] != kEmptyKeyDesc;
                     const float tK = full ? key_t(keys[K - 1]) : NINF;
-                    if (i0 && ex0 < tfl) i0 = false;
-                    if (i1 && ex1 < tfl) i1 = false;
-                    if (i0 && ex0 < tK) { i0 = false; floor_key = max(floor_key, pack_key(ex0, kFloorJ)); }
-                    if (i1 && ex1 < tK) { i1 = false; floor_key = max(floor_key, pack_key(ex1, kFloorJ)); }
+#pragma unroll
+                    for (int c = 0; c < W; ++c) {
+                        if (in[c] && x[c] < tfl) in[c] = false;
+                        if (in[c] && x[c] < tK) {
+                            in[c] = false;
+                            floor_key = max(floor_key, pack_key(x[c], kFloorJ));
+                        }
+                    }
                 }
                 float ev;
-                if (__any_sync(FULL, i0)) {
-                    const float xp = warp_max_nonneg(i0 ? ex0 : 0.f);  // ex0 >= tfl >= 0
-                    if (wq_push_evict<true>(q, xp, r0, lane, ev)) drop_floor(ev);
-                }
-                if (__any_sync(FULL, i1)) {
-                    const float xp = warp_max_nonneg(i1 ? ex1 : 0.f);
-                    if (wq_push_evict<true>(q, xp, r1, lane, ev)) drop_floor(ev);
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    if (__any_sync(FULL, in[c])) {
+                        const float xp = warp_max_nonneg(in[c] ? x[c] : 0.f);  // x >= tfl >= 0
+                        if (wq_push_evict<true>(q, xp, ch.ref[c], lane, ev)) drop_floor(ev);
+                    }
                 }
             }
             const float bound = wq_top<true>(q);  // -inf when empty: replay everything pending
@@ -1467,9 +1544,10 @@ __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int l
 template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
     extern __shared__ float4 s_top[];
-    for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    if (MODE != 3)
+        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0};
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -1490,9 +1568,12 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
         int count;
         float3 o, d;
         camera_ray(cam, px, py, o, d);
-        if (MODE == 2)
-            trace_forward_bf<K, COUNT>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count, cnt,
-                                       A.err);
+        if (MODE == 3)
+            trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+                                          cnt, A.err);
+        else if (MODE == 2)
+            trace_forward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+                                          cnt, A.err);
         else if (MODE == 1)
             trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                            cnt, A.err);
@@ -1528,9 +1609,10 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
 template <int K, bool PERSIST, bool COUNT, int MODE>
 __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
     extern __shared__ float4 s_top[];
-    for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    if (MODE != 3)
+        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0};
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -1561,8 +1643,10 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
             lk = A.skey[pix];
             if (COUNT) ++rays;
         }
-        if (MODE == 2)
-            trace_backward_bf<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+        if (MODE == 3)
+            trace_backward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+        else if (MODE == 2)
+            trace_backward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         else if (MODE == 1)
             trace_backward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
         else if (n > 0)
@@ -1691,6 +1775,7 @@ static int occupancy_of(bool backward, int block, size_t smem) {
 
 template <int K, bool COUNT>
 static int occupancy_m(bool backward, int block, int mode, size_t smem) {
+    if (mode == 3) return occupancy_of<K, true, COUNT, 3>(backward, block, 0);
     if (mode == 2) return occupancy_of<K, true, COUNT, 2>(backward, block, smem);
     if (mode == 1) return occupancy_of<K, true, COUNT, 1>(backward, block, smem);
     return occupancy_of<K, true, COUNT, 0>(backward, block, smem);
@@ -1710,7 +1795,7 @@ int persistent_grid(bool backward, int K, int block, bool count, int mode, int n
 
 template <int K, bool PERSIST, bool COUNT, int MODE>
 static void launch_one(bool backward, const FwdArgs& A, const BwdArgs* B, int grid, int block, cudaStream_t st) {
-    const size_t sm = smem_bytes(A.n_top);
+    const size_t sm = MODE == 3 ? 0 : smem_bytes(A.n_top);
     if (backward) k_render_bwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A, *B);
     else k_render_fwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A);
 }
@@ -1718,7 +1803,8 @@ static void launch_one(bool backward, const FwdArgs& A, const BwdArgs* B, int gr
 template <int K, bool PERSIST, bool COUNT>
 static void launch_mode(bool backward, const FwdArgs& A, const BwdArgs* B, int mode, int grid, int block,
                         cudaStream_t st) {
-    if (mode == 2) launch_one<K, PERSIST, COUNT, 2>(backward, A, B, grid, block, st);
+    if (mode == 3) launch_one<K, PERSIST, COUNT, 3>(backward, A, B, grid, block, st);
+    else if (mode == 2) launch_one<K, PERSIST, COUNT, 2>(backward, A, B, grid, block, st);
     else if (mode == 1) launch_one<K, PERSIST, COUNT, 1>(backward, A, B, grid, block, st);
     else launch_one<K, PERSIST, COUNT, 0>(backward, A, B, grid, block, st);
 }

@@ -35,6 +35,9 @@ struct rs_accel {
     int* counter = nullptr;
     float4* nodes = nullptr; // 4 per internal node (>= 1 node)
     float4* top = nullptr;   // 4 per staged node (kMaxSmemNodes), remapped copies of the top nodes
+    float4* wide = nullptr;  // 8 per internal node: 4-wide nodes (built when traversal == 3)
+    int has_wide = 0;
+    int64_t wide_cap = 0;
     int n_top = 0;           // staged nodes (0: no staging; the root is then node 0)
     int* err = nullptr;      // device error word
 };

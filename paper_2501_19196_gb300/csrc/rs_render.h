@@ -16,6 +16,7 @@ struct FwdArgs {
     const float4* nodes;
     const float4* top;    // staged top nodes (n_top of them; root = kTopRef when n_top > 0)
     int n_top;
+    const float4* wide;   // 4-wide nodes (traversal 3), 8 float4 per binary node index
     const DevCam* cams;
     int n_cams;
     int cam_single;       // >= 0: plain launch of this camera only; -1: persistent over all

@@ -48,7 +48,7 @@ def test_abi_version_and_default_tune(lib):
     from paper_2501_19196_gb300 import native
     assert lib.rs_abi_version() == 1
     t = native.default_tune()
-    assert (t.tile_w, t.tile_h, t.kbuf, t.leaf_size, t.morton_bits, t.traversal) == (8, 4, 32, 8, 21, 2)
+    assert (t.tile_w, t.tile_h, t.kbuf, t.leaf_size, t.morton_bits, t.traversal) == (8, 4, 32, 16, 21, 2)
 
 
 def test_host_validation_rejects_bad_arguments(lib):
@@ -65,7 +65,7 @@ def test_host_validation_rejects_bad_arguments(lib):
     # bad tile / kbuf / leaf / Q_box
     g = native.RsGaussians(10, 16, 16, 16, 16, 16)
     for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("morton_bits", 7), ("block_warps", 9),
-                       ("traversal", 3), ("smem_nodes", 513)):
+                       ("traversal", 4), ("smem_nodes", 513)):
         bad = native.default_tune(**{field: val})
         if field == "tile_w":
             bad.tile_h = 10

@@ -81,7 +81,8 @@ def test_gradients_invariant_to_tunables():
     prm = params(eps1=1e-3)
     for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16),
                dict(traversal=0), dict(traversal=0, kbuf=8, leaf_size=1), dict(traversal=2),
-               dict(traversal=2, kbuf=8, leaf_size=1), dict(smem_nodes=0), dict(smem_nodes=512, traversal=2)):
+               dict(traversal=2, kbuf=8, leaf_size=1), dict(smem_nodes=0), dict(smem_nodes=512, traversal=2),
+               dict(traversal=3), dict(traversal=3, kbuf=8, leaf_size=1)):
         errs, _ = _grad_case(sc, cams, prm, tune=native.default_tune(**kw))
         assert max(errs.values()) < TOL_GRAD, (kw, errs)
 

@@ -229,7 +229,8 @@ def test_tunables_and_launch_modes_bit_identical():
                dict(morton_bits=20), dict(traversal=0), dict(traversal=0, leaf_size=1, kbuf=8),
                dict(traversal=2), dict(traversal=2, leaf_size=1, kbuf=8), dict(traversal=2, persistent=0),
                dict(smem_nodes=0), dict(smem_nodes=512), dict(smem_nodes=1, traversal=2),
-               dict(smem_nodes=3, traversal=0),
+               dict(smem_nodes=3, traversal=0), dict(traversal=3), dict(traversal=3, leaf_size=1, kbuf=8),
+               dict(traversal=3, leaf_size=16, kbuf=16), dict(traversal=3, persistent=0),
                dict(block_warps=1), dict(block_warps=2)):
         out = gpu_render(sc, cams, prm, tune=native.default_tune(**kw))
         for k in ("rgb", "alpha", "depth"):
@@ -266,6 +267,17 @@ def test_misses_give_background_and_inside_camera_misses():
     sc = _single((0.0, 0.0, 0.05), (1.0, 1.0, 1.0))
     g = gpu_render(sc, scenes.look_at_camera((0, 0, 0), (0, 0, 1), 8, 8, 60), prm)
     np.testing.assert_array_equal(g["alpha"], 0.0)
+
+
+def test_single_gaussian_scene_in_every_traversal_mode():
+    sc = _single((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))
+    cam = scenes.look_at_camera((0, 0, -4), (0, 0, 0), 9, 9, 30)
+    from paper_2501_19196_gb300 import native
+    ref = gpu_render(sc, cam, params(), tune=native.default_tune(traversal=0))
+    for tr in (1, 2, 3):
+        out = gpu_render(sc, cam, params(), tune=native.default_tune(traversal=tr))
+        for k in ("rgb", "alpha", "depth"):
+            np.testing.assert_array_equal(out[k], ref[k])
 
 
 def test_invalid_render_arguments_are_rejected():
