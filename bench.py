@@ -34,7 +34,9 @@ L2_FLUSH_BYTES = 256 << 20
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, scaled to a
 # full launch (see profiles/); valid only while the kernel source hash matches.
-TRAFFIC = {"render.cu": None, "fwd_bytes": None, "bwd_bytes": None}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one ncu capture,
+# profiles/k_render_dram_traffic_1m_gaussians_16cams.md); reported only while render.cu is unchanged.
+TRAFFIC = {"render.cu": "bd9af387f06dca74", "fwd_bytes": 664.31e6, "bwd_bytes": 1114.23e6}
 
 
 def parse():
@@ -54,6 +56,7 @@ def parse():
     p.add_argument("--leaf", type=int, default=None)
     p.add_argument("--tile-w", type=int, default=None)
     p.add_argument("--traversal", type=int, default=None)
+    p.add_argument("--hit-list", type=int, default=None, help="per-ray hit-list capacity (0: adjoint re-traverses)")
     p.add_argument("--smem-nodes", type=int, default=None)
     p.add_argument("--profile", action="store_true",
                    help="ncu mode: `warmup` eager batched steps, then one more step, then exit (no JSON)")
@@ -244,6 +247,8 @@ def run_ours(args):
         overrides["traversal"] = args.traversal
     if args.smem_nodes is not None:
         overrides["smem_nodes"] = args.smem_nodes
+    if args.hit_list is not None:
+        overrides["hit_list"] = args.hit_list
     tune_b = native.default_tune(persistent=1, **overrides)
     tune_p = native.default_tune(persistent=0, **overrides)
     n = wl.scene.n
@@ -373,10 +378,15 @@ def run_ours(args):
     rb.check_device()
     sf = dict(zip(native.STATS_FIELDS, stats_f.cpu().tolist()))
     sb = dict(zip(native.STATS_FIELDS, stats_b.cpu().tolist()))
-    # algorithmic bytes per launch: node 64 B, test record 48 B, shade 16 B,
-    # outputs + state 36 B per ray; backward: replayed hit 64 B record + 64 B atomics, 32 B per ray
-    fwd_bytes = 64 * sf["nodes_visited"] + 48 * sf["gaussians_tested"] + 16 * sf["hits_composited"] + 36 * sf["rays"]
-    bwd_bytes = 64 * sb["nodes_visited"] + 48 * sb["gaussians_tested"] + 128 * sb["hits_composited"] + 32 * sb["rays"]
+    # algorithmic bytes per launch: node 64 B, test record 48 B, shade 16 B, outputs + state
+    # 36 B per ray, 4 B per hit-list id written; backward: replayed hit 64 B record + 64 B
+    # atomics, 4 B per id read from a hit list, 32 B per ray.  A re-traversed ray had more hits
+    # than the list holds, so the forward wrote a full list for it.
+    ids_written = sb["hits_listed"] + tune_b.hit_list * sb["rays_retraced"] if tune_b.hit_list > 0 else 0
+    fwd_bytes = (64 * sf["nodes_visited"] + 48 * sf["gaussians_tested"] + 16 * sf["hits_composited"] +
+                 36 * sf["rays"] + 4 * ids_written)
+    bwd_bytes = (64 * sb["nodes_visited"] + 48 * sb["gaussians_tested"] + 128 * sb["hits_composited"] +
+                 4 * sb["hits_listed"] + 32 * sb["rays"])
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     dom = "bwd" if kms["bwd"] >= kms["fwd"] else "fwd"

@@ -137,7 +137,14 @@ typedef struct {
  *                   distributed over the warp's registers); 3: as 2 over 4-wide nodes (each
  *                   binary node's grandchildren; rs_build_accel builds them when given 3)
  *   smem_nodes      0..512: the top BVH nodes (breadth first) that rs_build_accel stages for
- *                   the render kernels' shared memory (64 B each); 0 disables staging */
+ *                   the render kernels' shared memory (64 B each); 0 disables staging
+ *   hit_list        0..4096: rs_render records the sorted ids of each ray's first hit_list
+ *                   composited hits (4 B each, hit_list * 4 B per ray in the state), and the
+ *                   adjoint replays every ray with at most hit_list hits from that list instead
+ *                   of re-traversing the BVH (the paper's index buffer, Sec. 3 and 5); rays
+ *                   with more hits re-traverse (none when k_max <= hit_list, the paper's
+ *                   setting).  0: every ray re-traverses.  The adjoint follows the setting of
+ *                   the rs_render it differentiates. */
 typedef struct {
     int32_t tile_w, tile_h;
     int32_t kbuf;
@@ -147,6 +154,7 @@ typedef struct {
     int32_t block_warps;
     int32_t traversal;
     int32_t smem_nodes;
+    int32_t hit_list;
 } rs_tune_params;
 
 typedef struct rs_accel rs_accel;
@@ -160,7 +168,8 @@ typedef struct {
     uint64_t hits_composited;  /* composited hits (16 B shade record each) */
     uint64_t rounds;           /* k-buffer traversal rounds */
     uint64_t hits_inserted;    /* candidates inserted into a k-buffer */
-    uint64_t reserved[2];
+    uint64_t rays_retraced;    /* adjoint only: rays replayed by re-traversal (not from the list) */
+    uint64_t hits_listed;      /* adjoint only: hits replayed from the hit list */
 } rs_render_stats;
 
 /* ABI version (RS_ABI_VERSION of the build). */
@@ -170,7 +179,8 @@ int32_t rs_abi_version(void);
 const char* rs_last_error(void);
 
 /* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 16, 63-bit codes,
- * persistent launch, 4 warps per CTA, best-first warp-packet traversal, 256 staged nodes). */
+ * persistent launch, 4 warps per CTA, best-first warp-packet traversal, 256 staged nodes,
+ * hit lists of 256 ids per ray). */
 rs_status rs_default_tune(rs_tune_params* out);
 
 /* Build the acceleration structure of a scene (LBVH): per-Gaussian render records
@@ -179,14 +189,16 @@ rs_status rs_default_tune(rs_tune_params* out);
  * binary radix tree with leaves of at most leaf_size Gaussians, and a bottom-up box refit.
  * Q_box > 0 bounds the Q of every rs_render that uses this accel.  *inout: NULL to create,
  * else reused.  The accel reads the scene at build time only; rebuild after the parameters
- * change. */
+ * change.  On failure a newly created handle is freed (*inout stays NULL); a reused handle
+ * stays valid but holds no build until a later call succeeds. */
 rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_params* tune,
                          rs_accel** inout, void* cuda_stream);
 
 /* Render n_cams cameras (host array) of the scene `g` through `accel` (built from the same
  * scene).  Writes out->rgb / alpha / depth and, in *inout_state (NULL to create, else reused),
  * what the backward pass needs: per ray the final transmittance, the (t1, id) key of the
- * last composited hit and the hit count (16 B per ray), plus the cameras and parameters. */
+ * last composited hit and the hit count (16 B per ray), plus the cameras and parameters.
+ * On failure a reused state holds no render (rs_render_backward rejects it). */
 rs_status rs_render(const rs_gaussians* g, const rs_accel* accel, const rs_camera* cams,
                     int32_t n_cams, const rs_render_params* params, const rs_tune_params* tune,
                     rs_frame* out, rs_fwd_state** inout_state, void* cuda_stream);
@@ -200,16 +212,17 @@ rs_status rs_render_counted(const rs_gaussians* g, const rs_accel* accel, const 
                             void* cuda_stream);
 
 /* Adjoint of the last rs_render recorded in `state` (App. A.3-A.6): replays every ray back
- * to front (re-traversing `accel`), recovers the transmittance from the stored final value,
- * and ACCUMULATES dL/d(means, quats, scales, opacities, rgb) into `out`.  `g` and `accel`
- * must be the ones the forward pass used. */
+ * to front (from its hit list, or by re-traversing `accel`; see hit_list), recovers the
+ * transmittance from the stored final value, and ACCUMULATES dL/d(means, quats, scales,
+ * opacities, rgb) into `out`.  `g` and `accel` must be the ones the forward pass used. */
 rs_status rs_render_backward(const rs_gaussians* g, const rs_accel* accel,
                              const rs_fwd_state* state, const rs_frame_grad* dl,
                              const rs_tune_params* tune, rs_gaussian_grads* out,
                              void* cuda_stream);
 
-/* rs_render_backward plus per-call counters of the replay traversal (same layout as
- * rs_render_counted: rays, nodes visited, tests, replayed hits, rounds, inserted). */
+/* rs_render_backward plus per-call counters of the replay (same layout as rs_render_counted:
+ * rays, nodes visited, tests, replayed hits, rounds, inserted, rays re-traversed, hits
+ * replayed from the list). */
 rs_status rs_render_backward_counted(const rs_gaussians* g, const rs_accel* accel,
                                      const rs_fwd_state* state, const rs_frame_grad* dl,
                                      const rs_tune_params* tune, rs_gaussian_grads* out,
@@ -286,6 +299,15 @@ rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays,
 rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o,
                         const float* ray_d, const int32_t* sorted_j, float Q, float t_near,
                         float* out, void* cuda_stream);
+
+/* Allocation-failure injection, for tests of the out-of-memory paths (the paper has no
+ * counterpart).  With n > 0 the n-th device allocation the library makes from now on fails
+ * with RS_ERR_OOM (no cudaMalloc is attempted) and the hook disarms itself; n = 0 disarms it.
+ * Process-wide and not thread-safe; n < 0 returns RS_ERR_INVALID_ARG.  A call that fails this
+ * way leaves its handle unusable but valid: rs_render / rs_render_backward reject it with
+ * RS_ERR_INVALID_ARG until a later rs_build_accel / rs_render succeeds on it, and the
+ * *_destroy functions free it. */
+rs_status rs_test_fail_alloc(int64_t n);
 
 #ifdef __cplusplus
 }

@@ -63,7 +63,7 @@ typedef struct {
  *   TIE       two consecutive hits with |t1 - t1'| < OR_TIE_REL max(1, t) (up to the hit after
  *             the stop),
  *   EPS1      the transmittance after some composited hit within 1e-4 relative of eps1,
- *   TNEAR     a hit candidate with t1 within 1e-6 max(1, t) of t_near.
+ *   TNEAR     a hit candidate with t1 within OR_TIE_REL max(1, t) of t_near.
  * IMPACT is set when one of those alternative decisions (toggle the boundary Gaussian, swap
  * the tied pair, flip the eps1 stop) changes the ray's RGB or alpha by more than
  * OR_IMPACT_TOL; only such pixels have no unique correct value at the parity tolerance. */

@@ -32,12 +32,23 @@ rs_status cuda_check(const char* what) {
     return RS_OK;
 }
 
+// Allocation-failure injection (rs_test_fail_alloc): when armed with n > 0, the n-th device
+// allocation from then on fails with RS_ERR_OOM instead of calling cudaMalloc, and the hook disarms.
+static int64_t g_fail_alloc_in = 0;
+static bool injected_alloc_failure() {
+    if (g_fail_alloc_in <= 0) return false;
+    return --g_fail_alloc_in == 0;
+}
+
 // (re)allocate a device buffer of `count` elements, freeing the previous one
 template <typename T>
 static rs_status dmalloc(T*& p, int64_t count) {
     if (p) cudaFree(p);
     p = nullptr;
     if (count <= 0) count = 1;
+    if (injected_alloc_failure())
+        return set_error(RS_ERR_OOM, "injected allocation failure (rs_test_fail_alloc) of %lld bytes",
+                         (long long)(sizeof(T) * count));
     if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * (size_t)count) != cudaSuccess) {
         cudaGetLastError();
         return set_error(RS_ERR_OOM, "cudaMalloc of %lld bytes failed", (long long)(sizeof(T) * count));
@@ -69,6 +80,8 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
     if (t->traversal < 0 || t->traversal > 3)
         return set_error(RS_ERR_INVALID_ARG, "traversal %d: must be 0 (per ray), 1 (warp packet), 2 (best-first "
                          "warp packet) or 3 (best-first warp packet over 4-wide nodes)", t->traversal);
+    if (t->hit_list < 0 || t->hit_list > kMaxHitList)
+        return set_error(RS_ERR_INVALID_ARG, "hit_list %d: must be 0..%d", t->hit_list, kMaxHitList);
     return RS_OK;
 }
 
@@ -104,6 +117,13 @@ rs_status rs_default_tune(rs_tune_params* out) {
     out->block_warps = 4;
     out->traversal = 2;
     out->smem_nodes = 256;
+    out->hit_list = 256;
+    return RS_OK;
+}
+
+rs_status rs_test_fail_alloc(int64_t n) {
+    if (n < 0) return set_error(RS_ERR_INVALID_ARG, "n = %lld must be >= 0", (long long)n);
+    g_fail_alloc_in = n;
     return RS_OK;
 }
 
@@ -122,6 +142,9 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
         if (!A) return set_error(RS_ERR_OOM, "host allocation failed");
         cudaGetDevice(&A->device);
         if ((st = dmalloc(A->bounds, 6)) || (st = dmalloc(A->err, 1)) || (st = dmalloc(A->top, 4 * kMaxSmemNodes))) {
+            if (A->bounds) cudaFree(A->bounds);
+            if (A->err) cudaFree(A->err);
+            if (A->top) cudaFree(A->top);
             delete A;
             return st;
         }
@@ -129,6 +152,7 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
         *inout = A;
     }
     const int64_t n = g->n;
+    A->n = 0;  // unusable until this build succeeds (a failed (re)allocation leaves buffers missing)
     if (n > A->cap) {
         const int64_t cap = n;
         const int64_t nb = (cap + 2047) / 2048;
@@ -155,7 +179,9 @@ rs_status rs_build_accel(const rs_gaussians* g, float Q_box, const rs_tune_param
     A->leaf_size = tune->leaf_size;
     A->morton_bits = tune->morton_bits;
     A->Q_box = Q_box;
-    return build_accel_device(*A, *g, *tune, s);
+    st = build_accel_device(*A, *g, *tune, s);
+    if (st) A->n = 0;
+    return st;
 }
 
 static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const rs_camera* cams, int32_t n_cams,
@@ -216,18 +242,29 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         if (!S) return set_error(RS_ERR_OOM, "host allocation failed");
         cudaGetDevice(&S->device);
         if ((st = dmalloc(S->queue, 2)) || (st = dmalloc(S->err, 1))) {
+            if (S->queue) cudaFree(S->queue);
+            if (S->err) cudaFree(S->err);
             delete S;
             return st;
         }
         cudaMemset(S->err, 0, sizeof(int));
         *inout_state = S;
     }
+    S->n_pix = 0;  // holds no render until this forward is launched
     if (pix > S->cap_pix) {
         if ((st = dmalloc(S->sT, pix)) || (st = dmalloc(S->skey, pix)) || (st = dmalloc(S->sn, pix))) {
             S->cap_pix = 0;
             return st;
         }
         S->cap_pix = pix;
+    }
+    const int64_t n_ids = pix * tune->hit_list;
+    if (n_ids > S->cap_ids) {
+        if ((st = dmalloc(S->ids, n_ids))) {
+            S->cap_ids = 0;
+            return st;
+        }
+        S->cap_ids = n_ids;
     }
     if (n_cams > S->cap_cams) {
         if (S->cams_pinned) cudaFreeHost(S->cams_pinned);
@@ -255,7 +292,6 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
             return cuda_check("camera upload");
         S->cams_host = table;
     }
-    S->n_pix = pix;
     S->n_cams = n_cams;
     S->total_tiles = tiles;
     S->tile_w = tw;
@@ -274,6 +310,10 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     P.k_max = p->k_max;
     P.max_rounds = (int32_t)std::min<int64_t>(INT32_MAX, g->n / tune->kbuf + 3);
     P.max_visits = (int32_t)std::min<int64_t>(INT32_MAX, 2 * g->n + 16);
+    P.n_gauss = (int32_t)g->n;
+    P.n_nodes = (int32_t)std::max<int64_t>(1, g->n - 1);
+    P.list_cap = tune->hit_list;
+    P.ids = tune->hit_list > 0 ? S->ids : nullptr;
     S->P = P;
 
     FwdArgs A{};
@@ -317,6 +357,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
             if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "render launch: %s", cudaGetErrorString(e));
         }
     }
+    S->n_pix = pix;
     return RS_OK;
 }
 
@@ -435,7 +476,7 @@ rs_status rs_accel_destroy(rs_accel* A) {
 rs_status rs_state_destroy(rs_fwd_state* S) {
     if (!S) return RS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->gtmp, S->queue, S->err};
+    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->ids, S->gtmp, S->queue, S->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (S->cams_pinned) cudaFreeHost(S->cams_pinned);
@@ -460,9 +501,10 @@ rs_status rs_check_device(const rs_accel* accel, const rs_fwd_state* state, void
     if (st) return st;
     const int w = words[0] | words[1];
     if (w) {
-        return set_error(RS_ERR_INTERNAL, "device check failed (bits 0x%x:%s%s%s%s)", w,
+        return set_error(RS_ERR_INTERNAL, "device check failed (bits 0x%x:%s%s%s%s%s)", w,
                          (w & kErrReplayMismatch) ? " replay-mismatch" : "", (w & kErrBadScene) ? " bad-scene" : "",
-                         (w & kErrStack) ? " stack-overflow" : "", (w & kErrLoopGuard) ? " loop-guard" : "");
+                         (w & kErrStack) ? " stack-overflow" : "", (w & kErrLoopGuard) ? " loop-guard" : "",
+                         (w & kErrIndex) ? " index-out-of-range" : "");
     }
     return RS_OK;
 }
@@ -471,6 +513,7 @@ rs_status rs_accel_export(const rs_accel* A, int64_t* n_out, uint64_t* codes, ui
                           int32_t* last, int32_t* split, float* boxes, float* prim_boxes, float* lo_hi) {
     g_err[0] = 0;
     if (!A) return set_error(RS_ERR_INVALID_ARG, "accel is NULL");
+    if (A->n < 1) return set_error(RS_ERR_INVALID_ARG, "accel holds no successful build");
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_check("synchronize");
     const int64_t n = A->n;
     if (n_out) *n_out = n;
@@ -532,8 +575,8 @@ rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays, c
 rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o, const float* ray_d,
                         const int32_t* sorted_j, float Q, float t_near, float* out, void* cuda_stream) {
     g_err[0] = 0;
-    if (!accel || n_pairs < 0 || (n_pairs > 0 && (!ray_o || !ray_d || !sorted_j || !out)))
-        return set_error(RS_ERR_INVALID_ARG, "bad arguments");
+    if (!accel || accel->n < 1 || n_pairs < 0 || (n_pairs > 0 && (!ray_o || !ray_d || !sorted_j || !out)))
+        return set_error(RS_ERR_INVALID_ARG, "bad arguments (or an accel without a successful build)");
     if (n_pairs == 0) return RS_OK;
     const cudaError_t e =
         launch_debug_hits(accel->rec, accel->n, n_pairs, ray_o, ray_d, sorted_j, Q, t_near, out, (cudaStream_t)cuda_stream);

@@ -204,6 +204,10 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     F.P.k_max = p->k_max;
     F.P.max_rounds = (int32_t)(g->n / tune->kbuf + 3);
     F.P.max_visits = (int32_t)(2 * g->n + 16);
+    F.P.n_gauss = (int32_t)g->n;
+    F.P.n_nodes = (int32_t)std::max<int64_t>(1, g->n - 1);
+    F.P.list_cap = 0;  // forward only: no hit list
+    F.P.ids = nullptr;
     F.rgb = out->rgb;
     F.alpha = out->alpha;
     F.depth = out->depth;

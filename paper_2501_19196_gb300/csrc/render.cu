@@ -50,7 +50,16 @@ struct NodeSrc {
     const float4* s;
     int root;
     const float4* __restrict__ w;  // 4-wide nodes (8 float4 each), indexed like the binary nodes
+    int n_nodes, n_top, n_gauss;   // bounds of node references, staged slots and leaf ranges
+    int* err;
 };
+
+// a leaf's Gaussian count after the range check (a corrupt range reads nothing and is reported)
+__device__ __forceinline__ int leaf_count(const NodeSrc& ns, int start, int cnt) {
+    if (start >= 0 && cnt >= 0 && start <= ns.n_gauss - cnt) return cnt;
+    atomicOr(ns.err, kErrIndex);
+    return 0;
+}
 
 // The children of one node as seen by the traversal: W = 2 reads a binary node (possibly staged
 // in shared memory), W = 4 a wide node (the node's grandchildren; empty slots have ref kEmptyRef).
@@ -62,6 +71,13 @@ struct Children {
 
 __device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& n0, float4& n1, float4& n2,
                                            float4& n3) {
+    const bool ok = node >= kTopRef ? (node - kTopRef) < ns.n_top : (node >= 0 && node < ns.n_nodes);
+    if (!ok) {  // corrupt reference: report, and present a node without children
+        atomicOr(ns.err, kErrIndex);
+        n0 = n1 = n2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        n3 = make_float4(__int_as_float(kEmptyRef), __int_as_float(kEmptyRef), __int_as_float(0), __int_as_float(0));
+        return;
+    }
     if (node >= kTopRef) {
         const float4* p = ns.s + 4 * (node - kTopRef);
         n0 = p[0];
@@ -92,6 +108,16 @@ __device__ __forceinline__ void fetch_children<2>(const NodeSrc& ns, int node, C
 
 template <>
 __device__ __forceinline__ void fetch_children<4>(const NodeSrc& ns, int node, Children<4>& ch) {
+    if (node < 0 || node >= ns.n_nodes) {
+        atomicOr(ns.err, kErrIndex);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            ch.ref[c] = kEmptyRef;
+            ch.cnt[c] = 0;
+            ch.lo[0][c] = ch.lo[1][c] = ch.lo[2][c] = ch.hi[0][c] = ch.hi[1][c] = ch.hi[2][c] = 0.f;
+        }
+        return;
+    }
     const float4* p = ns.w + 8 * node;
     const float4 lx = __ldg(p + 0), hx = __ldg(p + 1), ly = __ldg(p + 2), hy = __ldg(p + 3);
     const float4 lz = __ldg(p + 4), hz = __ldg(p + 5), rf = __ldg(p + 6), ct = __ldg(p + 7);
@@ -195,7 +221,7 @@ struct Counters {
 // ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
 __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
-                                              const TraceParams& P, const float3 o, const float3 d, float& C0,
+                                              const TraceParams& P, int64_t pix, const float3 o, const float3 d, float& C0,
                                               float& C1, float& C2, float& T, float& depth,
                                               int64_t& last_key, int& count, Counters& cnt, int* err) {
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -239,6 +265,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
             C2 = fmaf(w, sh.w, C2);
             depth = fmaf(w, key_t(key), depth);
             T = __fmul_rn(T, __fsub_rn(1.f, a));
+            if (count < P.list_cap) P.ids[pix * P.list_cap + count] = j;  // for the adjoint's list replay
             ++count;
             last_key = key;
             if (COUNT) cnt.hits++;
@@ -274,7 +301,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                 const bool hs = side ? h1 : h0;
                 const int rr = side ? r1 : r0;
                 if (hs && rr < 0) {
-                    const int start = ~rr, num = side ? c1 : c0;
+                    const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
                         if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
                         const float4 g0 = __ldg(rec + 4 * q + 0);
@@ -465,7 +492,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                 const bool hs = side ? h1 : h0;
                 const int rr = side ? r1 : r0;
                 if (hs && rr < 0) {
-                    const int start = ~rr, num = side ? c1 : c0;
+                    const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
                         if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
                         const float4 g0 = __ldg(rec + 4 * q + 0);
@@ -608,6 +635,80 @@ __device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int
     }
 }
 
+// Running state of one ray's back-to-front replay: the transmittance in front of the next hit
+// to replay and the colour / alpha composited behind it (App. A.4-A.5).
+struct Adjoint {
+    float Tn, U0, U1, U2, UA;
+};
+
+// The adjoint of one composited hit (sorted Gaussian j), given the hits behind it: recovers
+// T_i = T_{i+1} / (1 - alpha_i), forms dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A)),
+// advances U, and returns the 16-float contribution (dM rows + dm, dopacity + drgb) in v.
+// alpha comes from the same solve as in the forward pass, so it has the same bits.
+__device__ __forceinline__ void adjoint_hit(const float4* __restrict__ rec, int j, const float3 o, const float3 d,
+                                            const TraceParams& P, Adjoint& s, const float gC[3], float gA,
+                                            float4 (&v)[4]) {
+    const float4 g0 = __ldg(rec + 4 * j + 0);
+    const float4 g1 = __ldg(rec + 4 * j + 1);
+    const float4 g2 = __ldg(rec + 4 * j + 2);
+    const float4 sh = __ldg(rec + 4 * j + 3);
+    Hit h;
+    ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+    const float e = expf(__fmul_rn(-0.5f, h.D2));
+    const float a = __fmul_rn(sh.x, e);
+    const float om = __fsub_rn(1.f, a);
+    const float Ti = __fdiv_rn(s.Tn, om);
+    const float w = Ti * a;
+    const float dLda =
+        Ti * (gC[0] * (sh.y - s.U0) + gC[1] * (sh.z - s.U1) + gC[2] * (sh.w - s.U2) + gA * (1.f - s.UA));
+    s.U0 = fmaf(a, sh.y, om * s.U0);
+    s.U1 = fmaf(a, sh.z, om * s.U1);
+    s.U2 = fmaf(a, sh.w, om * s.U2);
+    s.UA = fmaf(om, s.UA, a);
+    s.Tn = Ti;
+    const float gD2 = -0.5f * a * dLda;
+    const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+    const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);  // dL/dm = -M^T (2 gD2 p)
+    const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+    const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+    v[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
+    v[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
+    v[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
+    v[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
+}
+
+// ---------------------------------------------------------------------------------------------
+// List replay (the paper's index-buffer adjoint, Sec. 3 and Sec. 5): the forward pass wrote
+// the sorted ids of each ray's first list_cap composited hits; a ray with n <= list_cap hits is
+// replayed from that list back to front, with no traversal.  The whole warp calls it
+// (converged); lanes with n = 0 only take part in the scatter.
+// ---------------------------------------------------------------------------------------------
+template <bool COUNT>
+__device__ __forceinline__ void replay_list(const float4* __restrict__ rec, const TraceParams& P, int64_t pix,
+                                            const float3 o, const float3 d, float T_final, int n, const float gC[3],
+                                            float gA, float4* __restrict__ gtmp, Counters& cnt, int* err) {
+    Adjoint s{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
+    const int* row = P.ids + (n > 0 ? pix * P.list_cap : 0);
+    int k = n > 0 ? n : 0;
+    while (__any_sync(0xffffffffu, k > 0)) {
+        int jout = -1;
+        float4 v[4];
+        if (k > 0) {
+            --k;
+            const int j = __ldg(row + k);
+            if (j >= 0 && j < P.n_gauss) {
+                adjoint_hit(rec, j, o, d, P, s, gC, gA, v);
+                jout = j;
+                if (COUNT) cnt.hits++;
+            } else {  // a corrupt list: report and stop this ray
+                atomicOr(err, kErrIndex);
+                k = 0;
+            }
+        }
+        scatter_grad_warp(gtmp, jout, v);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Warp-packet variants.  The 32 lanes of a warp (one ray tile) traverse together: the node
 // sequence is shared (uniform loads are broadcast, descent is decided by warp votes: a child
@@ -619,7 +720,7 @@ __device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int
 // ---------------------------------------------------------------------------------------------
 template <int K, bool COUNT>
 __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
-                                                     const TraceParams& P, bool valid, const float3 o,
+                                                     const TraceParams& P, int64_t pix, bool valid, const float3 o,
                                                      const float3 d, float& C0, float& C1, float& C2, float& T,
                                                      float& depth, int64_t& last_key, int& count, Counters& cnt,
                                                      int* err) {
@@ -666,6 +767,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
             C2 = fmaf(w, sh.w, C2);
             depth = fmaf(w, key_t(key), depth);
             T = __fmul_rn(T, __fsub_rn(1.f, a));
+            if (count < P.list_cap) P.ids[pix * P.list_cap + count] = j;  // for the adjoint's list replay
             ++count;
             last_key = key;
             if (COUNT) cnt.hits++;
@@ -701,7 +803,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                 const int rr = side ? r1 : r0;
                 const bool want = (side ? h1 : h0) && rr < 0;
                 if (__any_sync(FULL, want)) {
-                    const int start = ~rr, num = side ? c1 : c0;
+                    const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
                         if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
@@ -809,8 +911,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
     const float NINF = __int_as_float(0xff800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    float Tn = T_final;
-    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     int st_node[kStackSize];
@@ -834,34 +935,8 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
-            const float4 g0 = __ldg(rec + 4 * j + 0);
-            const float4 g1 = __ldg(rec + 4 * j + 1);
-            const float4 g2 = __ldg(rec + 4 * j + 2);
-            const float4 sh = __ldg(rec + 4 * j + 3);
-            Hit h;
-            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-            const float e = expf(__fmul_rn(-0.5f, h.D2));
-            const float a = __fmul_rn(sh.x, e);
-            const float om = __fsub_rn(1.f, a);
-            const float Ti = __fdiv_rn(Tn, om);
-            const float w = Ti * a;
-            const float dLda =
-                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
-            U0 = fmaf(a, sh.y, om * U0);
-            U1 = fmaf(a, sh.z, om * U1);
-            U2 = fmaf(a, sh.w, om * U2);
-            UA = fmaf(om, UA, a);
-            Tn = Ti;
-            const float gD2 = -0.5f * a * dLda;
-            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
-            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
-            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            adjoint_hit(rec, j, o, d, P, adj, gC, gA, vout);
             jout = j;
-            vout[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
-            vout[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
-            vout[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
-            vout[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
@@ -906,7 +981,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                 const int rr = side ? r1 : r0;
                 const bool want = (side ? h1 : h0) && rr < 0;
                 if (__any_sync(FULL, want)) {
-                    const int start = ~rr, num = side ? c1 : c0;
+                    const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
                         if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
@@ -1143,7 +1218,7 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
 
 template <int K, bool COUNT, int W>
 __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
-                                                 const TraceParams& P, bool valid, const float3 o, const float3 d,
+                                                 const TraceParams& P, int64_t pix, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
                                                  int64_t& last_key, int& count, Counters& cnt, int* err) {
     const unsigned FULL = 0xffffffffu;
@@ -1187,6 +1262,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             C2 = fmaf(w, sh.w, C2);
             depth = fmaf(w, key_t(key), depth);
             T = __fmul_rn(T, __fsub_rn(1.f, a));
+            if (count < P.list_cap) P.ids[pix * P.list_cap + count] = j;  // for the adjoint's list replay
             ++count;
             last_key = key;
             if (COUNT) cnt.hits++;
@@ -1258,7 +1334,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     const int rr = ch.ref[c];
                     const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
-                        const int start = ~rr, num = ch.cnt[c];
+                        const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
                         for (int qq = start; qq < start + num; ++qq) {
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
@@ -1332,8 +1408,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
     const float INF = __int_as_float(0x7f800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    float Tn = T_final;
-    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     while (__any_sync(FULL, remaining > 0)) {
@@ -1354,34 +1429,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
-            const float4 g0 = __ldg(rec + 4 * j + 0);
-            const float4 g1 = __ldg(rec + 4 * j + 1);
-            const float4 g2 = __ldg(rec + 4 * j + 2);
-            const float4 sh = __ldg(rec + 4 * j + 3);
-            Hit h;
-            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-            const float e = expf(__fmul_rn(-0.5f, h.D2));
-            const float a = __fmul_rn(sh.x, e);
-            const float om = __fsub_rn(1.f, a);
-            const float Ti = __fdiv_rn(Tn, om);
-            const float w = Ti * a;
-            const float dLda =
-                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
-            U0 = fmaf(a, sh.y, om * U0);
-            U1 = fmaf(a, sh.z, om * U1);
-            U2 = fmaf(a, sh.w, om * U2);
-            UA = fmaf(om, UA, a);
-            Tn = Ti;
-            const float gD2 = -0.5f * a * dLda;
-            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
-            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
-            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            adjoint_hit(rec, j, o, d, P, adj, gC, gA, vout);
             jout = j;
-            vout[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
-            vout[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
-            vout[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
-            vout[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
@@ -1458,7 +1507,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     const int rr = ch.ref[c];
                     const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
-                        const int start = ~rr, num = ch.cnt[c];
+                        const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
                         for (int qq = start; qq < start + num; ++qq) {
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
@@ -1547,7 +1596,8 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
     if (MODE != 3)
         for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide};
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
+                     A.P.n_gauss, A.err};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -1569,16 +1619,16 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
         float3 o, d;
         camera_ray(cam, px, py, o, d);
         if (MODE == 3)
-            trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+            trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
         else if (MODE == 2)
-            trace_forward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+            trace_forward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
         else if (MODE == 1)
-            trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+            trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                            cnt, A.err);
         else if (valid)
-            trace_forward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
+            trace_forward<K, COUNT>(A.rec, A.sph, ns, A.P, pix, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
         if (valid) {
             A.rgb[3 * pix + 0] = fmaf(T, A.P.bg[0], C0);
             A.rgb[3 * pix + 1] = fmaf(T, A.P.bg[1], C1);
@@ -1612,11 +1662,13 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
     if (MODE != 3)
         for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide};
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
+                     A.P.n_gauss, A.err};
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
-    uint32_t rays = 0;
+    uint32_t rays = 0, retraced = 0;
+    uint64_t listed_hits = 0;
     while (true) {
         if (PERSIST) {
             unsigned long long t = 0;
@@ -1643,26 +1695,37 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
             lk = A.skey[pix];
             if (COUNT) ++rays;
         }
+        // rays whose hits all fit in the forward's hit list are replayed from it; the others
+        // (and every ray when there is no list) re-traverse the tree
+        int nt = n;
+        if (A.P.list_cap > 0) {
+            const bool listed = n <= A.P.list_cap;
+            replay_list<COUNT>(A.rec, A.P, pix, o, d, Tf, listed ? n : 0, gC, gA, B.gtmp, cnt, A.err);
+            if (listed) nt = 0;
+            if (COUNT && listed) listed_hits += n;
+        }
+        if (COUNT && nt > 0) ++retraced;
         if (MODE == 3)
-            trace_backward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
         else if (MODE == 2)
-            trace_backward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
         else if (MODE == 1)
-            trace_backward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
-        else if (n > 0)
-            trace_backward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, n, gC, gA, B.gtmp, cnt, A.err);
+            trace_backward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
+        else if (nt > 0)
+            trace_backward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
         if (!PERSIST) break;
     }
     if (COUNT) {
-        unsigned long long v[6] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted};
+        unsigned long long v[8] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted, retraced,
+                                   listed_hits};
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < 8; ++k) {
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) atomicAdd(A.stats + k, v[k]);
+            for (int k = 0; k < 8; ++k) atomicAdd(A.stats + k, v[k]);
         }
     }
 }

@@ -23,7 +23,8 @@ namespace rs {
 // ---------------------------------------------------------------------------------------------
 
 constexpr int kStackSize = 96;
-constexpr int kMaxSmemNodes = 512;        // staged top nodes (64 B each) in shared memory
+constexpr int kMaxSmemNodes = 512;
+constexpr int kMaxHitList = 4096;         // largest per-ray hit list        // staged top nodes (64 B each) in shared memory
 constexpr int kTopRef = 0x40000000;       // node reference kTopRef + s = staged slot s
 constexpr int kEmptyRef = INT32_MIN;      // empty child slot of a wide node         // >= depth of a radix tree over 64-bit codes + 32-bit ids
 constexpr int64_t kEmptyKey = INT64_MAX;  // empty slot of an ascending k-buffer
@@ -34,7 +35,8 @@ enum : int {
     kErrReplayMismatch = 1,  // backward found a different number of hits than the forward
     kErrBadScene = 2,        // non-finite or non-positive scale / zero quaternion seen in prep
     kErrStack = 4,           // traversal stack overflow (cannot happen for kStackSize >= depth)
-    kErrLoopGuard = 8        // a traversal / round / refit loop exceeded its bound (corrupt tree)
+    kErrLoopGuard = 8,       // a traversal / round / refit loop exceeded its bound (corrupt tree)
+    kErrIndex = 16           // a node reference or leaf range out of bounds (corrupt tree)
 };
 
 struct DevCam {
@@ -52,6 +54,10 @@ struct TraceParams {
     int32_t k_max;
     int32_t max_rounds;    // guard: no ray needs more rounds than n / K + 2
     int32_t max_visits;    // guard: a round visits each of the < n nodes at most once
+    int32_t n_gauss;       // guard: leaf ranges lie in [0, n_gauss)
+    int32_t n_nodes;       // guard: node references lie in [0, n_nodes) (or the staged slots)
+    int32_t list_cap;      // hit list: ids of the first list_cap composited hits per ray (0: none)
+    int* ids;              // hit list storage, list_cap ints per pixel (pixel-major rows)
 };
 
 // (t1, sorted id) packed into one ordered 64-bit key; t1 >= 0 so its bit pattern orders as

@@ -65,6 +65,8 @@ struct rs_fwd_state {
     float* sT = nullptr;
     int64_t* skey = nullptr;
     int* sn = nullptr;
+    int* ids = nullptr;                 // hit lists (hit_list ids per pixel)
+    int64_t cap_ids = 0;
     float4* gtmp = nullptr;
     unsigned long long* queue = nullptr;
     int* err = nullptr;

@@ -45,13 +45,15 @@ class RsGaussianGrads(ctypes.Structure):
 
 class RsTuneParams(ctypes.Structure):
     _fields_ = [("tile_w", i32), ("tile_h", i32), ("kbuf", i32), ("leaf_size", i32), ("morton_bits", i32),
-                ("persistent", i32), ("block_warps", i32), ("traversal", i32), ("smem_nodes", i32)]
+                ("persistent", i32), ("block_warps", i32), ("traversal", i32), ("smem_nodes", i32),
+                ("hit_list", i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-STATS_FIELDS = ("rays", "nodes_visited", "gaussians_tested", "hits_composited", "rounds", "hits_inserted")
+STATS_FIELDS = ("rays", "nodes_visited", "gaussians_tested", "hits_composited", "rounds", "hits_inserted",
+                "rays_retraced", "hits_listed")
 
 # name -> (restype, argtypes)
 _SIGS = {
@@ -71,6 +73,7 @@ _SIGS = {
     "rs_accel_export": (i32, [P, P, P, P, P, P, P, P, P, P]),
     "rs_debug_rays": (i32, [P, i32, i64, P, P, P, P, P, P]),
     "rs_debug_hits": (i32, [P, i64, P, P, P, f32, f32, P, P]),
+    "rs_test_fail_alloc": (i32, [i64]),
 }
 
 _LIB = None

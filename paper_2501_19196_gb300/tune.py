@@ -23,12 +23,13 @@ def default_cache_path() -> str:
     return os.environ.get(CACHE_ENV, os.path.join(os.path.expanduser("~"), ".cache", "raysplats_tune.json"))
 
 
-def candidates(tiles=((8, 4), (4, 8)), kbufs=(8, 16, 32), leaves=(1, 2, 4), warps=(4,), morton=(20, 21),
-               traversal=(1,), persistent=1):
+def candidates(tiles=((8, 4), (4, 8)), kbufs=(16, 32), leaves=(8, 16), warps=(4,), morton=(20, 21),
+               traversal=(2,), persistent=1, hit_lists=(256,), smem_nodes=256):
     """The cross product of the given tunables (all persistent launches by default)."""
     out = []
-    for (tw, th), k, leaf, w, mb, tr in itertools.product(tiles, kbufs, leaves, warps, morton, traversal):
-        out.append(native.RsTuneParams(tw, th, k, leaf, mb, persistent, w, tr, 256))
+    for (tw, th), k, leaf, w, mb, tr, hl in itertools.product(tiles, kbufs, leaves, warps, morton, traversal,
+                                                                hit_lists):
+        out.append(native.RsTuneParams(tw, th, k, leaf, mb, persistent, w, tr, smem_nodes, hl))
     return out
 
 

@@ -48,7 +48,8 @@ def test_abi_version_and_default_tune(lib):
     from paper_2501_19196_gb300 import native
     assert lib.rs_abi_version() == 1
     t = native.default_tune()
-    assert (t.tile_w, t.tile_h, t.kbuf, t.leaf_size, t.morton_bits, t.traversal) == (8, 4, 32, 16, 21, 2)
+    assert (t.tile_w, t.tile_h, t.kbuf, t.leaf_size, t.morton_bits, t.traversal, t.hit_list) == \
+        (8, 4, 32, 16, 21, 2, 256)
 
 
 def test_host_validation_rejects_bad_arguments(lib):
@@ -65,7 +66,7 @@ def test_host_validation_rejects_bad_arguments(lib):
     # bad tile / kbuf / leaf / Q_box
     g = native.RsGaussians(10, 16, 16, 16, 16, 16)
     for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("morton_bits", 7), ("block_warps", 9),
-                       ("traversal", 4), ("smem_nodes", 513)):
+                       ("traversal", 4), ("smem_nodes", 513), ("hit_list", -1), ("hit_list", 4097)):
         bad = native.default_tune(**{field: val})
         if field == "tile_w":
             bad.tile_h = 10
@@ -81,6 +82,21 @@ def test_host_validation_rejects_bad_arguments(lib):
                                   ctypes.byref(out), None) == native.RS_ERR_INVALID_ARG
     # destroy accepts NULL
     assert lib.rs_accel_destroy(None) == 0 and lib.rs_state_destroy(None) == 0
+
+
+def test_injected_allocation_failure_frees_the_new_handle(lib):
+    """rs_test_fail_alloc(1): the first device allocation of a new accel fails before any CUDA
+    call, the half-built handle is freed and *inout stays NULL; the hook then disarms itself."""
+    from paper_2501_19196_gb300 import native
+    t = native.default_tune()
+    g = native.RsGaussians(10, 16, 16, 16, 16, 16)
+    acc = ctypes.c_void_p()
+    assert lib.rs_test_fail_alloc(-1) == native.RS_ERR_INVALID_ARG
+    assert lib.rs_test_fail_alloc(1) == native.RS_OK
+    assert lib.rs_build_accel(ctypes.byref(g), 11.3, ctypes.byref(t), ctypes.byref(acc), None) == native.RS_ERR_OOM
+    assert b"injected allocation failure" in lib.rs_last_error()
+    assert not acc
+    assert lib.rs_test_fail_alloc(0) == native.RS_OK
 
 
 def test_product_path_never_reaches_the_oracle():

@@ -79,12 +79,53 @@ def test_gradients_invariant_to_tunables():
     cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 40, 24, 55.0),
                                   scenes.look_at_camera((2.0, 2.0, -2.0), (0, 0, 0), 16, 40, 50.0)])
     prm = params(eps1=1e-3)
-    for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16),
-               dict(traversal=0), dict(traversal=0, kbuf=8, leaf_size=1), dict(traversal=2),
+    # the re-traversing adjoint of every traversal order and setting (hit_list = 0) ...
+    retrace = [dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16),
+               dict(traversal=0), dict(traversal=0, kbuf=8, leaf_size=1), dict(traversal=1),
                dict(traversal=2, kbuf=8, leaf_size=1), dict(smem_nodes=0), dict(smem_nodes=512, traversal=2),
-               dict(traversal=3), dict(traversal=3, kbuf=8, leaf_size=1)):
+               dict(traversal=3), dict(traversal=3, kbuf=8, leaf_size=1)]
+    # ... and hit lists: the default, tiny (most rays re-traverse), mixed, and the largest
+    listed = [dict(), dict(hit_list=1), dict(hit_list=3), dict(hit_list=3, traversal=0),
+              dict(hit_list=2, traversal=1), dict(hit_list=4, traversal=3), dict(hit_list=4096, persistent=0)]
+    for kw in [dict(kw, hit_list=0) for kw in retrace] + listed:
         errs, _ = _grad_case(sc, cams, prm, tune=native.default_tune(**kw))
         assert max(errs.values()) < TOL_GRAD, (kw, errs)
+
+
+def test_hit_list_split_counters():
+    """The adjoint replays a ray from its hit list exactly when the list holds all its hits:
+    with the largest list nothing re-traverses, without a list everything does, and in between
+    the listed and re-traversed hits add up to the forward's composited hits."""
+    from paper_2501_19196_gb300 import Renderer, native
+    sc = scenes.random_tiny_scene(78, n=400, spread=1.0, log_mu=-2.3)
+    cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 48, 32, 55.0)])
+    prm = params(eps1=1e-3)
+    rng = np.random.default_rng(3)
+    P = int(cams.total_rays())
+    d_rgb = torch.from_numpy(rng.standard_normal((P, 3)).astype(np.float32)).cuda()
+    seen = {}
+    for H in (0, 1, 4, 4096):
+        r = Renderer(tune=native.default_tune(hit_list=H))
+        r.build(*to_dev(sc))
+        sf = torch.zeros(8, dtype=torch.int64, device="cuda")
+        sb = torch.zeros(8, dtype=torch.int64, device="cuda")
+        r.render(cams, prm, stats=sf)
+        r.backward(d_rgb, stats=sb)
+        torch.cuda.synchronize()
+        r.check_device()
+        f = dict(zip(native.STATS_FIELDS, sf.cpu().tolist()))
+        b = dict(zip(native.STATS_FIELDS, sb.cpu().tolist()))
+        r.close()
+        assert b["hits_composited"] == f["hits_composited"] > 0
+        assert b["hits_listed"] <= H * (b["rays"] - b["rays_retraced"])
+        if H == 0:
+            assert b["hits_listed"] == 0 and b["rays_retraced"] == b["rays"]
+        if H == 4096:
+            assert b["rays_retraced"] == 0 and b["hits_listed"] == f["hits_composited"] and b["nodes_visited"] == 0
+        seen[H] = b
+    # more list capacity never re-traverses more rays
+    assert seen[0]["rays_retraced"] >= seen[1]["rays_retraced"] >= seen[4]["rays_retraced"] >= 0
+    assert 0 < seen[4]["hits_listed"] < seen[4096]["hits_listed"]
 
 
 def test_autograd_function_matches_direct_backward():

@@ -231,7 +231,8 @@ def test_tunables_and_launch_modes_bit_identical():
                dict(smem_nodes=0), dict(smem_nodes=512), dict(smem_nodes=1, traversal=2),
                dict(smem_nodes=3, traversal=0), dict(traversal=3), dict(traversal=3, leaf_size=1, kbuf=8),
                dict(traversal=3, leaf_size=16, kbuf=16), dict(traversal=3, persistent=0),
-               dict(block_warps=1), dict(block_warps=2)):
+               dict(block_warps=1), dict(block_warps=2), dict(hit_list=0), dict(hit_list=1),
+               dict(hit_list=4096, traversal=1)):
         out = gpu_render(sc, cams, prm, tune=native.default_tune(**kw))
         for k in ("rgb", "alpha", "depth"):
             np.testing.assert_array_equal(out[k], ref[k], err_msg=str(kw))
