@@ -32,11 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s fwd and fwd+bwd at 1M Gaussians, batched vs plain, at oracle tolerance"
 L2_FLUSH_BYTES = 256 << 20
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, scaled to a
-# full launch (see profiles/); valid only while the kernel source hash matches.
-# dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one ncu capture,
-# profiles/k_render_dram_traffic_1m_gaussians_16cams.md); reported only while render.cu is unchanged.
-TRAFFIC = {"render.cu": "bd9af387f06dca74", "fwd_bytes": 664.31e6, "bwd_bytes": 1114.23e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one capture,
+# profiles/k_render_dram_traffic_1m_gaussians_16cams.md): the forward kernel, and the hit-list
+# replay for the adjoint.  Reported only while render.cu is unchanged (hash).
+TRAFFIC = {"render.cu": "d323c8573f3c4390", "fwd_bytes": 5.52e9, "bwd_bytes": 5.22e9}
 
 
 def parse():
@@ -337,6 +336,19 @@ def run_ours(args):
     ms_f, _ = timed(g_f.replay, args.steps, args.warmup)
     rb.check_device()
     ms_fb_nograph, _ = timed(lambda: step(rb, True), max(3, args.steps // 2), 1)
+    # the adjoint without hit lists (every ray re-traverses the BVH), same graph-captured step
+    replay = None
+    if tune_b.hit_list > 0 and not args.no_plain:
+        rr = Renderer(tune=native.default_tune(**dict(tune_b.as_dict(), hit_list=0)), Q_box=wl.Q)
+        rr.set_cameras(wl.cams)
+        step(rr)
+        g_rr = capture(lambda: step(rr, True))
+        ms_rr, _ = timed(g_rr.replay, max(3, args.steps // 2), args.warmup)
+        rr.check_device()
+        del g_rr
+        rr.close()
+        replay = {"fwd_bwd_mrays_s": P / ms_rr / 1e3 * world, "ms_per_step_fwd_bwd": ms_rr,
+                  "adjoint": "re-traversal of every ray (hit_list 0)"}
     plain = {}
     if not args.no_plain:
         ms_p_fb, _ = timed(lambda: step(rp, True), max(3, args.steps // 2), 1)
@@ -344,7 +356,8 @@ def run_ours(args):
         rp.check_device()
         plain = {"fwd_bwd_mrays_s": P / ms_p_fb / 1e3 * world, "fwd_mrays_s": P / ms_p_f / 1e3 * world,
                  "ms_per_step_fwd_bwd": ms_p_fb, "ms_per_step_fwd": ms_p_f,
-                 "launches_per_step": "one forward and one backward launch per camera"}
+                 "launches_per_step": "one forward and one hit-list replay launch per camera, one "
+                                      "re-traversal launch over the overflow tiles"}
 
     # --- per-kernel durations (events on the launching stream), batched path ---
     kt = {"build": [], "fwd": [], "bwd": []}
@@ -396,8 +409,8 @@ def run_ours(args):
     if TRAFFIC.get("render.cu") == src_hash("render.cu"):
         traffic = TRAFFIC["bwd_bytes" if dom == "bwd" else "fwd_bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "k_render_bwd (persistent)" if dom == "bwd" else
-                "k_render_fwd (persistent)", "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": traffic, "kernel": "adjoint: k_replay_list + k_render_bwd + k_finalize" if dom == "bwd"
+                else "k_render_fwd (persistent)", "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": dom_bytes, "kernel_ms": kms[dom],
                 "counts_fwd": sf, "counts_bwd": sb,
                 "min_bytes_fraction": (64 * sf["hits_composited"] + 36 * sf["rays"]) / (kms["fwd"] * 1e-3) / 1e9 / hbm}
@@ -441,7 +454,9 @@ def run_ours(args):
 
     # bounds init, bounds, morton, 3 per sort pass, records, karras, refit, top-node staging
     launches_build = 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3 + (1 if tune_b.smem_nodes > 0 else 0)
-    gpu_launches = args.steps * (launches_build + 1 + 2)
+    # forward; adjoint: list replay + re-traversal of the overflow tiles (or one re-traversal
+    # launch without hit lists) + finalize
+    gpu_launches = args.steps * (launches_build + 1 + (3 if tune_b.hit_list > 0 else 2))
     value = P / ms_fb / 1e3 * world
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
@@ -449,7 +464,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "gaussians": n, "cameras": wl.cams.count, "rays_per_step": P,
                    "step": "LBVH rebuild + forward render + adjoint, all cameras",
-                   "path": "batched: one persistent forward and one persistent backward launch, CUDA graph",
+                   "path": "batched: one persistent forward launch; adjoint: one persistent hit-list replay "
+                           "launch and one persistent re-traversal launch over the overflow tiles; CUDA graph",
                    "tune": tune_b.as_dict(), "l2": "flushed between timed steps (256 MiB write, untimed)",
                    "parallelism": f"replicas x{world}"},
         "fwd_mrays_s": P / ms_f / 1e3 * world, "ms_per_step_fwd": ms_f,
@@ -457,6 +473,7 @@ def run_ours(args):
         "plain": plain,
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
         "kernel_ms": kms,
+        "adjoint_without_hit_lists": replay,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }

@@ -241,7 +241,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         S = new (std::nothrow) rs_fwd_state();
         if (!S) return set_error(RS_ERR_OOM, "host allocation failed");
         cudaGetDevice(&S->device);
-        if ((st = dmalloc(S->queue, 2)) || (st = dmalloc(S->err, 1))) {
+        if ((st = dmalloc(S->queue, 4)) || (st = dmalloc(S->err, 1))) {
             if (S->queue) cudaFree(S->queue);
             if (S->err) cudaFree(S->err);
             delete S;
@@ -399,6 +399,14 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         }
         S->cap_gauss = g->n;
     }
+    const bool list = S->P.list_cap > 0;  // the forward recorded hit lists
+    if (list && S->total_tiles > S->cap_ovf) {
+        if ((st = dmalloc(S->ovf, S->total_tiles))) {
+            S->cap_ovf = 0;
+            return st;
+        }
+        S->cap_ovf = S->total_tiles;
+    }
     if (cudaMemsetAsync(S->gtmp, 0, sizeof(float4) * 4 * (size_t)g->n, s) != cudaSuccess)
         return cuda_check("gradient scratch reset");
     FwdArgs A{};
@@ -419,13 +427,41 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
     A.err = accel->err;
     A.stats = reinterpret_cast<unsigned long long*>(stats);
     const bool count = stats != nullptr;
-    BwdArgs B{dl->d_rgb, dl->d_alpha, S->gtmp};
+    BwdArgs B{dl->d_rgb, dl->d_alpha, S->gtmp, list ? S->ovf : nullptr, list ? S->cap_ovf : 0};
     const int block = 32 * tune->block_warps;
-    if (tune->persistent) {
+    if (cudaMemsetAsync(S->queue + 1, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess)
+        return cuda_check("queue reset");
+    if (list) {
+        // 1. replay every ray whose hits fit in its list; collect the tiles that overflow
+        if (tune->persistent) {
+            A.cam_single = -1;
+            A.total_tiles = S->total_tiles;
+            const int grid = (int)std::min<int64_t>(list_replay_grid(count, block, sm_count()),
+                                                    (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
+            const cudaError_t e = launch_list_replay(A, B, true, count, std::max(grid, 1), block, s);
+            if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "list replay launch: %s", cudaGetErrorString(e));
+        } else {
+            for (int c = 0; c < S->n_cams; ++c) {
+                const DevCam& D = S->cams_host[(size_t)c];
+                A.cam_single = c;
+                A.total_tiles = (int64_t)D.tiles_x * D.tiles_y;
+                const int grid = (int)((A.total_tiles + tune->block_warps - 1) / tune->block_warps);
+                const cudaError_t e = launch_list_replay(A, B, false, count, grid, block, s);
+                if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "list replay launch: %s", cudaGetErrorString(e));
+            }
+        }
+        // 2. re-traverse the overflow tiles (a persistent launch over the device-side list)
         A.cam_single = -1;
         A.total_tiles = S->total_tiles;
-        if (cudaMemsetAsync(S->queue + 1, 0, sizeof(unsigned long long), s) != cudaSuccess)
-            return cuda_check("queue reset");
+        const int grid = (int)std::min<int64_t>(
+            persistent_grid(true, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
+            (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
+        const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
+                                              block, s);
+        if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "backward launch: %s", cudaGetErrorString(e));
+    } else if (tune->persistent) {
+        A.cam_single = -1;
+        A.total_tiles = S->total_tiles;
         const int grid = (int)std::min<int64_t>(
             persistent_grid(true, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
             (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
@@ -476,7 +512,7 @@ rs_status rs_accel_destroy(rs_accel* A) {
 rs_status rs_state_destroy(rs_fwd_state* S) {
     if (!S) return RS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->ids, S->gtmp, S->queue, S->err};
+    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->ids, S->gtmp, S->ovf, S->queue, S->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (S->cams_pinned) cudaFreeHost(S->cams_pinned);

@@ -1656,19 +1656,16 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
     }
 }
 
-template <int K, bool PERSIST, bool COUNT, int MODE>
-__global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
-    extern __shared__ float4 s_top[];
-    if (MODE != 3)
-        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
-    __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
-                     A.P.n_gauss, A.err};
+// List replay (adjoint, first launch): one warp per ray tile of the forward pass; every ray
+// whose hits all fit in its hit list is replayed from it (replay_list).  A tile holding a ray
+// with more hits is appended to the overflow list, which k_render_bwd re-traverses next.
+template <bool PERSIST, bool COUNT>
+__global__ void __launch_bounds__(128) k_replay_list(FwdArgs A, BwdArgs B) {
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
-    uint32_t rays = 0, retraced = 0;
-    uint64_t listed_hits = 0;
+    uint32_t rays = 0;
+    uint64_t listed = 0;
     while (true) {
         if (PERSIST) {
             unsigned long long t = 0;
@@ -1681,30 +1678,90 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
         int64_t pix;
         const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
         const int n = valid ? A.sn[pix] : 0;
+        const int nl = n <= A.P.list_cap ? n : 0;
+        float3 o, d;
+        camera_ray(cam, px, py, o, d);
+        float gC[3] = {0.f, 0.f, 0.f};
+        float gA = 0.f, Tf = 1.f;
+        if (nl > 0) {
+            gC[0] = B.d_rgb[3 * pix];
+            gC[1] = B.d_rgb[3 * pix + 1];
+            gC[2] = B.d_rgb[3 * pix + 2];
+            gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
+            Tf = A.sT[pix];
+        }
+        if (COUNT && n > 0) ++rays;
+        if (COUNT) listed += nl;
+        replay_list<COUNT>(A.rec, A.P, pix, o, d, Tf, nl, gC, gA, B.gtmp, cnt, A.err);
+        if (__any_sync(0xffffffffu, n > A.P.list_cap) && lane == 0) {
+            const int64_t global = A.cam_single < 0 ? tile : A.cams[A.cam_single].tile_base + tile;
+            const unsigned long long slot = atomicAdd(A.queue + 3, 1ull);
+            if (slot < (unsigned long long)B.ovf_cap) B.ovf[slot] = (int)global;
+            else atomicOr(A.err, kErrIndex);
+        }
+        if (!PERSIST) break;
+    }
+    if (COUNT) {
+        unsigned long long v[8] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (v[k]) atomicAdd(A.stats + k, v[k]);
+        }
+    }
+}
+
+template <int K, bool PERSIST, bool COUNT, int MODE>
+__global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
+    extern __shared__ float4 s_top[];
+    if (B.ovf && A.queue[3] == 0) return;  // every ray was replayed from its hit list
+    if (MODE != 3)
+        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    __syncthreads();
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
+                     A.P.n_gauss, A.err};
+    const int lane = threadIdx.x & 31;
+    // with a hit list, only the tiles the list replay found overflowing are re-traversed
+    const int64_t n_tiles = B.ovf ? (int64_t)min((unsigned long long)B.ovf_cap, A.queue[3]) : A.total_tiles;
+    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Counters cnt;
+    uint32_t rays = 0, retraced = 0;
+    while (true) {
+        if (PERSIST) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(A.queue + 2, 1ull);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (tile >= n_tiles) break;
+        if (B.ovf) tile = B.ovf[tile];
+        DevCam cam;
+        int px, py;
+        int64_t pix;
+        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
+        const int n = valid ? A.sn[pix] : 0;
+        const int nt = n > A.P.list_cap ? n : 0;  // rays the hit list cannot replay
         float3 o, d;
         camera_ray(cam, px, py, o, d);
         float gC[3] = {0.f, 0.f, 0.f};
         float gA = 0.f, Tf = 1.f;
         int64_t lk = -1;
-        if (n > 0) {
+        if (nt > 0) {
             gC[0] = B.d_rgb[3 * pix];
             gC[1] = B.d_rgb[3 * pix + 1];
             gC[2] = B.d_rgb[3 * pix + 2];
             gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
             Tf = A.sT[pix];
             lk = A.skey[pix];
-            if (COUNT) ++rays;
+            if (COUNT) {
+                ++retraced;
+                if (A.P.list_cap == 0) ++rays;
+            }
         }
-        // rays whose hits all fit in the forward's hit list are replayed from it; the others
-        // (and every ray when there is no list) re-traverse the tree
-        int nt = n;
-        if (A.P.list_cap > 0) {
-            const bool listed = n <= A.P.list_cap;
-            replay_list<COUNT>(A.rec, A.P, pix, o, d, Tf, listed ? n : 0, gC, gA, B.gtmp, cnt, A.err);
-            if (listed) nt = 0;
-            if (COUNT && listed) listed_hits += n;
-        }
-        if (COUNT && nt > 0) ++retraced;
         if (MODE == 3)
             trace_backward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
         else if (MODE == 2)
@@ -1716,8 +1773,7 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
         if (!PERSIST) break;
     }
     if (COUNT) {
-        unsigned long long v[8] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted, retraced,
-                                   listed_hits};
+        unsigned long long v[8] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted, retraced, 0};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
@@ -1899,6 +1955,30 @@ cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool pers
     else if (K == 16) launch_kp<16>(true, A, &B, persistent, count, mode, grid, block, st);
     else if (K == 32) launch_kp<32>(true, A, &B, persistent, count, mode, grid, block, st);
     else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <bool PERSIST, bool COUNT>
+static int list_occupancy(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_replay_list<PERSIST, COUNT>, block, 0);
+    return nb;
+}
+
+int list_replay_grid(bool count, int block, int sms) {
+    const int nb = count ? list_occupancy<true, true>(block) : list_occupancy<true, false>(block);
+    return std::max(1, nb) * sms;
+}
+
+cudaError_t launch_list_replay(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
+                               cudaStream_t st) {
+    if (persistent) {
+        if (count) k_replay_list<true, true><<<grid, block, 0, st>>>(A, B);
+        else k_replay_list<true, false><<<grid, block, 0, st>>>(A, B);
+    } else {
+        if (count) k_replay_list<false, true><<<grid, block, 0, st>>>(A, B);
+        else k_replay_list<false, false><<<grid, block, 0, st>>>(A, B);
+    }
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ struct FwdArgs {
     float* sT;        // per pixel: final transmittance
     int64_t* skey;    // per pixel: (t1, sorted id) key of the last composited hit
     int* sn;          // per pixel: composited hits
-    unsigned long long* queue;  // [0] forward tile counter, [1] backward tile counter
+    unsigned long long* queue;  // [0] forward tiles, [1] list-replay tiles, [2] re-traversal tiles,
+                                // [3] overflow tiles appended by the list replay
     int* err;
     unsigned long long* stats;
 };
@@ -38,9 +39,15 @@ struct BwdArgs {
     const float* d_rgb;
     const float* d_alpha;
     float4* gtmp;  // 4 per Gaussian (Morton order): (dM row k, dm_k) k = 0..2, (dop, drgb)
+    int* ovf;      // tiles (global ids) holding a ray with more hits than its hit list; NULL:
+                   // the re-traversing adjoint covers every tile
+    int64_t ovf_cap;
 };
 
 int persistent_grid(bool backward, int K, int block, bool count, int mode, int n_top, int sms);
+int list_replay_grid(bool count, int block, int sms);
+cudaError_t launch_list_replay(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
+                               cudaStream_t st);
 cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,
                            cudaStream_t st);
 cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
@@ -68,6 +75,8 @@ struct rs_fwd_state {
     int* ids = nullptr;                 // hit lists (hit_list ids per pixel)
     int64_t cap_ids = 0;
     float4* gtmp = nullptr;
+    int* ovf = nullptr;                 // overflow tile list of the adjoint
+    int64_t cap_ovf = 0;
     unsigned long long* queue = nullptr;
     int* err = nullptr;
     // what the forward recorded

@@ -163,11 +163,17 @@ def test_every_allocation_failure_is_reported_and_recoverable():
     else:
         pytest.fail("the forward never succeeded")
 
-    # 4. backward: its gradient scratch is the one allocation; the retry succeeds
-    lib.rs_test_fail_alloc(1)
-    c.oom(c.backward(acc, state))
-    lib.rs_test_fail_alloc(0)
-    native.check(c.backward(acc, state))
+    # 4. backward (gradient scratch, overflow tile list): each allocation fails in turn, then succeeds
+    for k in range(1, MAX_ALLOCS + 1):
+        lib.rs_test_fail_alloc(k)
+        st = c.backward(acc, state)
+        lib.rs_test_fail_alloc(0)
+        if st == native.RS_OK:
+            break
+        c.oom(st)
+    else:
+        pytest.fail("the backward never succeeded")
+    assert k >= 3
     imgs, grads = c.outputs()
     native.check(lib.rs_check_device(acc, state, c.stream))
     _same(imgs, grads, ref_imgs, ref_grads)
