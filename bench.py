@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--kbuf", type=int, default=None)
     p.add_argument("--leaf", type=int, default=None)
     p.add_argument("--tile-w", type=int, default=None)
+    p.add_argument("--morton-bits", type=int, default=None)
+    p.add_argument("--block-warps", type=int, default=None)
     p.add_argument("--traversal", type=int, default=None)
     p.add_argument("--hit-list", type=int, default=None, help="per-ray hit-list capacity (0: adjoint re-traverses)")
     p.add_argument("--smem-nodes", type=int, default=None)
@@ -242,6 +244,10 @@ def run_ours(args):
         overrides["leaf_size"] = args.leaf
     if args.tile_w:
         overrides["tile_w"] = args.tile_w
+    if args.morton_bits:
+        overrides["morton_bits"] = args.morton_bits
+    if args.block_warps:
+        overrides["block_warps"] = args.block_warps
     if args.traversal is not None:
         overrides["traversal"] = args.traversal
     if args.smem_nodes is not None:
@@ -380,8 +386,8 @@ def run_ours(args):
     kms = {k: sum(v) / len(v) for k, v in kt.items()}
 
     # --- traversal counters (instrumented kernels, same inputs) ---
-    stats_f = torch.zeros(8, dtype=torch.int64, device=dev)
-    stats_b = torch.zeros(8, dtype=torch.int64, device=dev)
+    stats_f = torch.zeros(10, dtype=torch.int64, device=dev)
+    stats_b = torch.zeros(10, dtype=torch.int64, device=dev)
     rb.build(*params)
     rb.render(None, prm, out=outs, stats=stats_f)
     for t in grads.values():

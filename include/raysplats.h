@@ -170,6 +170,10 @@ typedef struct {
     uint64_t hits_inserted;    /* candidates inserted into a k-buffer */
     uint64_t rays_retraced;    /* adjoint only: rays replayed by re-traversal (not from the list) */
     uint64_t hits_listed;      /* adjoint only: hits replayed from the hit list */
+    uint64_t warp_node_fetches;    /* packet traversals: nodes fetched by whole warps; lane
+                                      efficiency = nodes_visited / (32 * warp_node_fetches) */
+    uint64_t warp_leaf_iterations; /* packet traversals: leaf-loop iterations of whole warps;
+                                      lane efficiency = gaussians_tested / (32 * this) */
 } rs_render_stats;
 
 /* ABI version (RS_ABI_VERSION of the build). */
@@ -203,7 +207,7 @@ rs_status rs_render(const rs_gaussians* g, const rs_accel* accel, const rs_camer
                     int32_t n_cams, const rs_render_params* params, const rs_tune_params* tune,
                     rs_frame* out, rs_fwd_state** inout_state, void* cuda_stream);
 
-/* rs_render plus per-call counters: *stats_device (device memory, 8 uint64, zeroed by the
+/* rs_render plus per-call counters: *stats_device (device memory, 10 uint64, zeroed by the
  * caller) is incremented with the rs_render_stats fields.  Slower; for measurement only. */
 rs_status rs_render_counted(const rs_gaussians* g, const rs_accel* accel, const rs_camera* cams,
                             int32_t n_cams, const rs_render_params* params,

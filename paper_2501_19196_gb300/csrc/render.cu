@@ -205,6 +205,7 @@ __device__ __forceinline__ void kbuf_pop_front(int64_t (&keys)[K], int64_t empty
 
 struct Counters {
     uint32_t nodes = 0, tests = 0, hits = 0, rounds = 0, inserted = 0;
+    uint32_t wnodes = 0, wleaf = 0;  // packet modes: node fetches and leaf iterations of whole warps
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -783,6 +784,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
             float4 n0, n1, n2, n3;
             fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT && active) cnt.nodes++;
+            if (COUNT && (threadIdx.x & 31) == 0) cnt.wnodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
             const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
@@ -805,6 +807,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                 if (__any_sync(FULL, want)) {
                     const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
+                        if (COUNT && (threadIdx.x & 31) == 0) cnt.wleaf++;
                         if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
                             const float4 g1 = __ldg(rec + 4 * q + 1);
@@ -962,6 +965,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
             float4 n0, n1, n2, n3;
             fetch_node(nodes, node, n0, n1, n2, n3);
             if (COUNT && active) cnt.nodes++;
+            if (COUNT && (threadIdx.x & 31) == 0) cnt.wnodes++;
             float en0, ex0, en1, ex1;
             slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
             const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
@@ -983,6 +987,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                 if (__any_sync(FULL, want)) {
                     const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
                     for (int q = start; q < start + num; ++q) {
+                        if (COUNT && (threadIdx.x & 31) == 0) cnt.wleaf++;
                         if (want && sphere_may_hit(o, d, __ldg(sph + q))) {
                             const float4 g0 = __ldg(rec + 4 * q + 0);
                             const float4 g1 = __ldg(rec + 4 * q + 1);
@@ -1307,6 +1312,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                 Children<W> ch;
                 fetch_children<W>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
+                if (COUNT && lane == 0) cnt.wnodes++;
                 float e[W], x[W];
                 bool h[W];
 #pragma unroll
@@ -1336,6 +1342,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
                         for (int qq = start; qq < start + num; ++qq) {
+                            if (COUNT && lane == 0) cnt.wleaf++;
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
@@ -1482,6 +1489,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 Children<W> ch;
                 fetch_children<W>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
+                if (COUNT && lane == 0) cnt.wnodes++;
                 float en[W], x[W];
                 bool h[W];
 #pragma unroll
@@ -1509,6 +1517,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
                         for (int qq = start; qq < start + num; ++qq) {
+                            if (COUNT && lane == 0) cnt.wleaf++;
                             if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
@@ -1643,15 +1652,17 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
         if (!PERSIST) break;
     }
     if (COUNT) {
-        unsigned long long v[6] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted};
+        unsigned long long v[kNumStats] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds,
+                                           cnt.inserted, 0, 0, cnt.wnodes, cnt.wleaf};
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < kNumStats; ++k) {
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) atomicAdd(A.stats + k, v[k]);
+            for (int k = 0; k < kNumStats; ++k)
+                if (v[k]) atomicAdd(A.stats + k, v[k]);
         }
     }
 }
@@ -1702,15 +1713,15 @@ __global__ void __launch_bounds__(128) k_replay_list(FwdArgs A, BwdArgs B) {
         if (!PERSIST) break;
     }
     if (COUNT) {
-        unsigned long long v[8] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed};
+        unsigned long long v[kNumStats] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed, 0, 0};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kNumStats; ++k) {
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
+            for (int k = 0; k < kNumStats; ++k)
                 if (v[k]) atomicAdd(A.stats + k, v[k]);
         }
     }
@@ -1773,15 +1784,16 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
         if (!PERSIST) break;
     }
     if (COUNT) {
-        unsigned long long v[8] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds, cnt.inserted, retraced, 0};
+        unsigned long long v[kNumStats] = {rays,     cnt.nodes, cnt.tests, cnt.hits,   cnt.rounds,
+                                           cnt.inserted, retraced, 0,        cnt.wnodes, cnt.wleaf};
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < kNumStats; ++k) {
 #pragma unroll
             for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
         }
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) atomicAdd(A.stats + k, v[k]);
+            for (int k = 0; k < kNumStats; ++k) atomicAdd(A.stats + k, v[k]);
         }
     }
 }

@@ -24,7 +24,8 @@ namespace rs {
 
 constexpr int kStackSize = 96;
 constexpr int kMaxSmemNodes = 512;
-constexpr int kMaxHitList = 4096;         // largest per-ray hit list        // staged top nodes (64 B each) in shared memory
+constexpr int kMaxHitList = 4096;         // largest per-ray hit list
+constexpr int kNumStats = 10;             // uint64 counters of rs_render_stats        // staged top nodes (64 B each) in shared memory
 constexpr int kTopRef = 0x40000000;       // node reference kTopRef + s = staged slot s
 constexpr int kEmptyRef = INT32_MIN;      // empty child slot of a wide node         // >= depth of a radix tree over 64-bit codes + 32-bit ids
 constexpr int64_t kEmptyKey = INT64_MAX;  // empty slot of an ascending k-buffer

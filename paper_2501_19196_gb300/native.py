@@ -53,7 +53,7 @@ class RsTuneParams(ctypes.Structure):
 
 
 STATS_FIELDS = ("rays", "nodes_visited", "gaussians_tested", "hits_composited", "rounds", "hits_inserted",
-                "rays_retraced", "hits_listed")
+                "rays_retraced", "hits_listed", "warp_node_fetches", "warp_leaf_iterations")
 
 # name -> (restype, argtypes)
 _SIGS = {

@@ -107,8 +107,8 @@ def test_hit_list_split_counters():
     for H in (0, 1, 4, 4096):
         r = Renderer(tune=native.default_tune(hit_list=H))
         r.build(*to_dev(sc))
-        sf = torch.zeros(8, dtype=torch.int64, device="cuda")
-        sb = torch.zeros(8, dtype=torch.int64, device="cuda")
+        sf = torch.zeros(10, dtype=torch.int64, device="cuda")
+        sb = torch.zeros(10, dtype=torch.int64, device="cuda")
         r.render(cams, prm, stats=sf)
         r.backward(d_rgb, stats=sb)
         torch.cuda.synchronize()
