@@ -29,7 +29,7 @@ IMP_BOUNDARY, IMP_TIE, IMP_EPS1 = 32, 64, 128
 
 class OrParams(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_double), ("eps1", ctypes.c_double), ("t_near", ctypes.c_double),
-                ("bg", ctypes.c_double * 3), ("k_max", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("bg", ctypes.c_double * 3), ("k_max", ctypes.c_int32), ("sort_key", ctypes.c_int32)]
 
 
 def lib():
@@ -40,7 +40,7 @@ def lib():
         P = ctypes.c_void_p
         i64, i32 = ctypes.c_int64, ctypes.c_int32
         L.or_render.restype = ctypes.c_int
-        L.or_render.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P, P, P, P, P, P, P, P,
+        L.or_render.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P,
                                 P, P, P, i32]
         L.or_raygen_f32.restype = None
         L.or_raygen_f32.argtypes = [P, i64, P, P, P, P, P]
@@ -113,10 +113,13 @@ def quat_to_rot(q):
 
 
 def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background=(0, 0, 0),
-                t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, params64=None):
+                t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, params64=None, sort_key=0,
+                dl_depth=None):
     """Render explicit rays.  `scene` fields are converted to float64 exactly (or taken from
-    `params64`, a dict of float64 arrays, for finite differences).  Returns a dict with rgb
-    (R,3), alpha, depth, T, n_hits, mask and, when dl_rgb is given, the float64 gradients."""
+    `params64`, a dict of float64 arrays, for finite differences).  sort_key 0 orders hits by
+    the entry t1, 1 by the maximum-response parameter t_m.  Returns a dict with rgb (R,3),
+    alpha, depth, T, n_hits, mask and, when dl_rgb or dl_depth is given, the float64
+    gradients of <dl_rgb, rgb> + <dl_alpha, alpha> + <dl_depth, depth>."""
     src = params64 if params64 is not None else {
         "means": scene.means, "quats": scene.quats, "scales": scene.scales,
         "opacities": scene.opacities, "rgb": scene.rgb}
@@ -126,19 +129,22 @@ def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background
     ray_o, ray_d = _c(ray_o, np.float64), _c(ray_d, np.float64)
     R = ray_o.shape[0]
     prm = OrParams(float(Q), float(eps1), float(t_near), (ctypes.c_double * 3)(*background),
-                   int(k_max), 0)
+                   int(k_max), int(sort_key))
     out = {"rgb": np.zeros((R, 3)), "alpha": np.zeros(R), "depth": np.zeros(R),
            "T": np.zeros(R), "n_hits": np.zeros(R, np.int32), "mask": np.zeros(R, np.int32)}
     grads = None
+    if dl_rgb is None and dl_depth is not None:
+        dl_rgb = np.zeros((R, 3))
     if dl_rgb is not None:
         dl_rgb = _c(dl_rgb, np.float64)
         dl_alpha = None if dl_alpha is None else _c(dl_alpha, np.float64)
+        dl_depth = None if dl_depth is None else _c(dl_depth, np.float64)
         grads = {"means": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "scales": np.zeros((n, 3)),
                  "opacities": np.zeros(n), "rgb": np.zeros((n, 3))}
     rc = lib().or_render(
         n, _p(means), _p(quats), _p(scales), _p(opac), _p(rgb), R, _p(ray_o), _p(ray_d),
         ctypes.byref(prm), _p(out["rgb"]), _p(out["alpha"]), _p(out["depth"]), _p(out["T"]),
-        _p(out["n_hits"]), _p(out["mask"]), _p(dl_rgb), _p(dl_alpha),
+        _p(out["n_hits"]), _p(out["mask"]), _p(dl_rgb), _p(dl_alpha), _p(dl_depth),
         *(_p(grads[k]) if grads else None for k in ("means", "quats", "scales", "opacities", "rgb")),
         int(threads or default_threads()))
     if rc != 0:
@@ -149,10 +155,11 @@ def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background
 
 
 def render(scene, cams, ray_cam, px, py, Q, eps1=1e-4, k_max=2 ** 31 - 1, background=(0, 0, 0),
-           t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None):
+           t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, sort_key=0, dl_depth=None):
     """Render the listed pixels (camera index, x, y) with FP32-defined rays."""
     o, d = raygen_f32(cams, ray_cam, px, py)
-    return render_rays(scene, o, d, Q, eps1, k_max, background, t_near, dl_rgb, dl_alpha, threads)
+    return render_rays(scene, o, d, Q, eps1, k_max, background, t_near, dl_rgb, dl_alpha, threads,
+                       sort_key=sort_key, dl_depth=dl_depth)
 
 
 def morton(means, bits, scales=None):

@@ -25,11 +25,14 @@
  *   - the norm in Prop. 2 is the SQUARED Mahalanobis distance D^2 (Gaussian definition);
  *   - Prop. 1's root uses sqrt(a (Q - D^2)) / a (the appendix form);
  *   - <o',d'> >= 0 takes the first branch; a ray is a hit at D^2 == Q (inclusive);
- *   - hits are ordered by (t1, index) ascending; the hit that brings T below eps1 is
- *     composited, then the ray stops; at most k_max hits are composited;
- *   - RGB = C + T_final * background, alpha = 1 - T_final, depth = sum w_i t1_i;
- *   - the gradient is the exact derivative of that output with the hit set, order and
- *     cut point held fixed (the paper's eps2 phase is a different estimator, not this one).
+ *   - hits are ordered by (t_key, index) ascending, where t_key is the entry t1 (sort key 0)
+ *     or the parameter t_m of the maximum response (sort key 1, the chord midpoint); the hit
+ *     that brings T below eps1 is composited, then the ray stops; at most k_max hits are
+ *     composited;
+ *   - RGB = C + T_final * background, alpha = 1 - T_final, depth = sum w_i t_key_i;
+ *   - the gradient is the exact derivative of those outputs (depth included) with the hit
+ *     set, order and cut point held fixed (the paper's eps2 phase is a different estimator,
+ *     not this one).
  */
 #include <math.h>
 #include <pthread.h>
@@ -54,7 +57,7 @@ typedef struct {
     double t_near;   /* rays start at t_near (>= 0) */
     double bg[3];    /* background colour */
     int32_t k_max;   /* at most k_max composited hits per ray */
-    int32_t pad;
+    int32_t sort_key; /* 0: order hits by entry t1; 1: by t_m, the maximum-response parameter */
 } or_params;
 
 /* Ambiguity flags (per ray).  FP32 and FP64 may legitimately take a different discrete
@@ -260,7 +263,7 @@ typedef struct {
     double *out_rgb, *out_alpha, *out_depth, *out_T;
     int32_t *out_nhits, *out_mask;
     /* gradient inputs */
-    const double *dl_rgb, *dl_alpha;
+    const double *dl_rgb, *dl_alpha, *dl_depth;
     /* work split */
     int64_t r0, r1;
     /* per-thread gradient contributions */
@@ -295,10 +298,11 @@ static void push_contrib(or_job* J, int64_t idx, const double v[14]) {
  * dD2/d(box) = 2 <p, do'/d(box)> - 2 tau <p, dd'/d(box)>. */
 static void ray_gradient(or_job* J, const double o[3], const double d[3], const or_hit* hits,
                          int nh, const double* alpha, const double* T, const double* gc,
-                         double ga) {
+                         double ga, double gd) {
     const double* bg = J->prm->bg;
+    const double Q = J->prm->Q;
     double U[3] = {bg[0], bg[1], bg[2]};
-    double UA = 0.0;
+    double UA = 0.0, UD = 0.0; /* alpha and depth seen behind hit i (background depth 0) */
     for (int h = nh - 1; h >= 0; --h) {
         const int64_t i = hits[h].idx;
         const double* c = J->rgb + 3 * i;
@@ -307,11 +311,14 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
         memset(v, 0, sizeof(v));
         /* colour */
         for (int ch = 0; ch < 3; ++ch) v[11 + ch] = gc[ch] * Ti * a;
-        /* dL/dalpha */
-        double dLda = ga * Ti * (1.0 - UA);
+        /* dL/dalpha; depth is composited like a colour channel with value t_key */
+        const double tk = hits[h].t;
+        double dLda = ga * Ti * (1.0 - UA) + gd * Ti * (tk - UD);
         for (int ch = 0; ch < 3; ++ch) dLda += gc[ch] * Ti * (c[ch] - U[ch]);
         for (int ch = 0; ch < 3; ++ch) U[ch] = a * c[ch] + (1.0 - a) * U[ch];
         UA = a + (1.0 - a) * UA;
+        UD = a * tk + (1.0 - a) * UD;
+        const double dLdt = gd * Ti * a; /* depth = sum w_i t_key_i, w_i = T_i alpha_i */
         /* geometry */
         const double* m = J->means + 3 * i;
         const double* q = J->quats + 4 * i;
@@ -322,6 +329,12 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
         const double e = exp(-0.5 * g.D2);
         v[10] = dLda * e;                         /* d opacity */
         const double dLdD2 = -0.5 * a * dLda;     /* alpha = opacity exp(-D2/2) */
+        /* t_key as a function of (o', d'): t_m = -tau = -b/a and t1 = t_m - r with
+         * r = sqrt((Q - D2)/a), so
+         *   dt_m = -db/a + tau da/a,  dt1 = dt_m + dD2/(2 r a) + (Q - D2) da/(2 r a^2),
+         * with da = 2<d', dd'>, db = <do', d'> + <o', dd'> and dD2 as below. */
+        const int use_tm = J->prm->sort_key == 1;
+        const double rr = sqrt(fmax(Q - g.D2, 0.0) / g.a);
         /* dD2/dbox = 2<p, do'> - 2 tau <p, dd'> */
         double om[3] = {o[0] - m[0], o[1] - m[1], o[2] - m[2]};
         /* means: do'/dm_x = -M e_x, dd'/dm_x = 0 */
@@ -329,11 +342,24 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
             double dop[3] = {-M[x], -M[3 + x], -M[6 + x]};
             double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]);
             v[x] = dLdD2 * dD2;
+            if (dLdt != 0.0) {
+                const double db = dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2];
+                const double dtm = -db / g.a; /* da = 0 */
+                v[x] += dLdt * (use_tm ? dtm : dtm + dD2 / (2.0 * rr * g.a));
+            }
         }
         /* scales: do'/ds_k = -(1/s_k) o'_k e_k, dd'/ds_k = -(1/s_k) d'_k e_k */
         for (int k = 0; k < 3; ++k) {
             double dD2 = 2.0 * g.p[k] * (-g.op[k] / s[k]) - 2.0 * g.tau * g.p[k] * (-g.dp[k] / s[k]);
             v[7 + k] = dLdD2 * dD2;
+            if (dLdt != 0.0) {
+                const double dop_k = -g.op[k] / s[k], ddp_k = -g.dp[k] / s[k];
+                const double da = 2.0 * g.dp[k] * ddp_k;
+                const double db = dop_k * g.dp[k] + g.op[k] * ddp_k;
+                const double dtm = -db / g.a + g.tau * da / g.a;
+                const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
+                v[7 + k] += dLdt * (use_tm ? dtm : dt1);
+            }
         }
         /* quaternion: do'/dq_x = S^-1 (dR/dq_x)^T (o - m), dd'/dq_x = S^-1 (dR/dq_x)^T d */
         double dR[4][9];
@@ -350,6 +376,14 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
             double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]) -
                          2.0 * g.tau * (g.p[0] * ddp[0] + g.p[1] * ddp[1] + g.p[2] * ddp[2]);
             v[3 + x] = dLdD2 * dD2;
+            if (dLdt != 0.0) {
+                const double da = 2.0 * (g.dp[0] * ddp[0] + g.dp[1] * ddp[1] + g.dp[2] * ddp[2]);
+                const double db = (dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2]) +
+                                  (g.op[0] * ddp[0] + g.op[1] * ddp[1] + g.op[2] * ddp[2]);
+                const double dtm = -db / g.a + g.tau * da / g.a;
+                const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
+                v[3 + x] += dLdt * (use_tm ? dtm : dt1);
+            }
         }
         push_contrib(J, i, v);
     }
@@ -432,7 +466,7 @@ static void* render_worker(void* arg) {
             const int inside = g.D2 <= Q;
             const int is_hit = inside && g.t1 >= P->t_near;
             if (is_hit) {
-                hits[nh].t = g.t1;
+                hits[nh].t = P->sort_key == 1 ? -g.tau : g.t1;
                 hits[nh].idx = i;
                 hits[nh].D2 = g.D2;
                 nh++;
@@ -440,7 +474,7 @@ static void* render_worker(void* arg) {
             const int near_bd = fabs(Q - g.D2) < OR_BOUNDARY_REL * Q && g.t1 >= P->t_near;
             const int near_tn = inside && fabs(g.t1 - P->t_near) < OR_TIE_REL * fmax(1.0, fabs(g.t1));
             if (near_bd || near_tn) {
-                cand[nc].t = g.t1 > P->t_near ? g.t1 : P->t_near;
+                cand[nc].t = P->sort_key == 1 ? -g.tau : (g.t1 > P->t_near ? g.t1 : P->t_near);
                 cand[nc].idx = i;
                 cand[nc].D2 = g.D2;
                 cand_kind[nc] = (near_bd ? OR_AMB_BOUNDARY : 0) | (near_tn ? OR_AMB_TNEAR : 0);
@@ -519,7 +553,8 @@ static void* render_worker(void* arg) {
         if (J->dl_rgb) {
             const double* gc = J->dl_rgb + 3 * r;
             const double ga = J->dl_alpha ? J->dl_alpha[r] : 0.0;
-            ray_gradient(J, o, d, hits, (int)count, alpha, T, gc, ga);
+            const double gd = J->dl_depth ? J->dl_depth[r] : 0.0;
+            ray_gradient(J, o, d, hits, (int)count, alpha, T, gc, ga, gd);
         }
     }
     free(hits);
@@ -535,15 +570,18 @@ static void* render_worker(void* arg) {
  * Render n_rays rays (ray_o/ray_d, 3 doubles each) against n Gaussians (FP64 parameters;
  * quats (w,x,y,z) unnormalised, scales physical > 0, opacities in (0,1)).
  * Outputs per ray: rgb[3], alpha, depth, T_final, n_hits, ambiguity mask.
- * If dl_rgb != NULL, the gradients of sum_r <dl_rgb[r], rgb[r]> + dl_alpha[r] alpha[r]
- * are ADDED into g_means[3n], g_quats[4n], g_scales[3n], g_opac[n], g_rgb[3n].
+ * If dl_rgb != NULL, the gradients of
+ *   sum_r <dl_rgb[r], rgb[r]> + dl_alpha[r] alpha[r] + dl_depth[r] depth[r]
+ * (dl_alpha, dl_depth may be NULL) are ADDED into g_means[3n], g_quats[4n], g_scales[3n],
+ * g_opac[n], g_rgb[3n].
  * Returns 0 on success, -1 on allocation failure.
  */
 int or_render(int64_t n, const double* means, const double* quats, const double* scales,
               const double* opac, const double* rgb, int64_t n_rays, const double* ray_o,
               const double* ray_d, const or_params* prm, double* out_rgb, double* out_alpha,
               double* out_depth, double* out_T, int32_t* out_nhits, int32_t* out_mask,
-              const double* dl_rgb, const double* dl_alpha, double* g_means, double* g_quats,
+              const double* dl_rgb, const double* dl_alpha, const double* dl_depth, double* g_means,
+              double* g_quats,
               double* g_scales, double* g_opac, double* g_rgb, int32_t nthreads) {
     if (nthreads < 1) nthreads = 1;
     if (n_rays < nthreads) nthreads = (int32_t)(n_rays > 0 ? n_rays : 1);
@@ -562,7 +600,7 @@ int or_render(int64_t n, const double* means, const double* quats, const double*
         J->rgb = rgb; J->M = M; J->n_rays = n_rays; J->ray_o = ray_o; J->ray_d = ray_d;
         J->prm = prm; J->out_rgb = out_rgb; J->out_alpha = out_alpha; J->out_depth = out_depth;
         J->out_T = out_T; J->out_nhits = out_nhits; J->out_mask = out_mask;
-        J->dl_rgb = dl_rgb; J->dl_alpha = dl_alpha;
+        J->dl_rgb = dl_rgb; J->dl_alpha = dl_alpha; J->dl_depth = dl_depth;
         J->r0 = n_rays * t / nthreads;
         J->r1 = n_rays * (t + 1) / nthreads;
     }

@@ -421,6 +421,83 @@ def test_gradient_matches_central_differences(seed, flat):
         assert err < 1e-6, (key, err)
 
 
+@pytest.mark.parametrize("sort_key", [0, 1])
+@pytest.mark.parametrize("seed,flat", [(41, 0.0), (42, 0.5)])
+def test_depth_gradient_matches_central_differences(seed, flat, sort_key):
+    """Depth = sum w_i t_key_i: its gradient (colour-like through alpha, plus dt_key/dparams)
+    against FP64 central differences, for both sort keys, together with rgb and alpha terms."""
+    sc = scenes.random_tiny_scene(seed, n=10, spread=0.4, log_mu=-1.5, flat_frac=flat)
+    o, d = _tiny_rays(8, seed)
+    rng = np.random.default_rng(seed)
+    R = o.shape[0]
+    gc = rng.standard_normal((R, 3))
+    ga = rng.standard_normal(R)
+    gd = rng.standard_normal(R)
+    kw = dict(Q=Q99, eps1=1e-3, background=(0.2, 0.4, 0.6), sort_key=sort_key)
+    base = oracle.render_rays(sc, o, d, **kw)
+    ok = base["mask"] == 0
+    gc[~ok], ga[~ok], gd[~ok] = 0.0, 0.0, 0.0
+    base = oracle.render_rays(sc, o, d, dl_rgb=gc, dl_alpha=ga, dl_depth=gd, **kw)
+    P = {k: getattr(sc, k).astype(np.float64).copy() for k in ("means", "quats", "scales", "opacities", "rgb")}
+
+    def loss(params):
+        out = oracle.render_rays(None, o, d, params64=params, **kw)
+        return float(np.sum(out["rgb"] * gc) + np.sum(out["alpha"] * ga) + np.sum(out["depth"] * gd))
+
+    for key in P:
+        fd = np.zeros_like(P[key])
+        flat_view = P[key].reshape(-1)
+        for j in range(flat_view.size):
+            x = flat_view[j]
+            h = 1e-6 * max(1.0, abs(x))
+            flat_view[j] = x + h
+            lp = loss(P)
+            flat_view[j] = x - h
+            lm = loss(P)
+            flat_view[j] = x
+            fd.reshape(-1)[j] = (lp - lm) / (2 * h)
+        an = base["grads"][key]
+        err = np.linalg.norm(an - fd) / max(np.linalg.norm(fd), 1e-300)
+        assert err < 1e-6, (key, err)
+
+
+def test_sort_key_tm_closed_forms():
+    """Isotropic Gaussians (Eq. 8, Prop. 1): t_m is the parameter of the closest approach to
+    the mean, <m - o, d>, and t1 = t_m - s sqrt(Q - rho^2/s^2); the depth follows the key."""
+    sigma, op = 0.3, 0.8
+    for rho in (0.0, 0.5, 1.7):
+        s32 = float(np.float32(sigma))
+        sc = scenes.Scene(np.array([[0.0, 0.0, 0.25]], np.float32), np.array([[0.3, 0.4, -0.5, 0.2]], np.float32),
+                          np.full((1, 3), sigma, np.float32), np.array([op], np.float32),
+                          np.ones((1, 3), np.float32))
+        o = np.array([[rho * s32, 0.0, -5.0]])
+        d = np.array([[0.0, 0.0, 1.0]])
+        a = float(np.float32(op)) * math.exp(-rho * rho / 2)
+        tm = 5.25
+        t1 = tm - s32 * math.sqrt(Q99 - rho * rho)
+        out0 = oracle.render_rays(sc, o, d, Q99, sort_key=0)
+        out1 = oracle.render_rays(sc, o, d, Q99, sort_key=1)
+        assert abs(out0["depth"][0] - a * t1) < 1e-12
+        assert abs(out1["depth"][0] - a * tm) < 1e-12
+        np.testing.assert_allclose(out0["rgb"], out1["rgb"], atol=0)
+
+
+def test_sort_key_changes_the_compositing_order():
+    """A large Gaussian whose entry comes first but whose centre lies behind a small one:
+    ordered by t1 it is composited first, by t_m second (Eq. 3 with the two orders)."""
+    means = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 0.6]], np.float32)   # big (behind), small
+    scales = np.array([[0.4, 0.4, 0.4], [0.02, 0.02, 0.02]], np.float32)
+    ops = np.array([0.5, 0.7], np.float32)
+    cols = np.array([[1, 0, 0], [0, 0, 1]], np.float32)
+    sc = scenes.Scene(means, np.tile(np.array([[1, 0, 0, 0]], np.float32), (2, 1)), scales, ops, cols)
+    o, d = np.array([[0.0, 0.0, -3.0]]), np.array([[0.0, 0.0, 1.0]])
+    a = [float(x) for x in ops]
+    big_first = a[0] * cols[0] + (1 - a[0]) * a[1] * cols[1]
+    small_first = a[1] * cols[1] + (1 - a[1]) * a[0] * cols[0]
+    np.testing.assert_allclose(oracle.render_rays(sc, o, d, Q99, sort_key=0)["rgb"][0], big_first, atol=1e-14)
+    np.testing.assert_allclose(oracle.render_rays(sc, o, d, Q99, sort_key=1)["rgb"][0], small_first, atol=1e-14)
+
+
 # ----------------------------------------------------------------------------------------
 # Acceleration-structure references (plain definitions)
 # ----------------------------------------------------------------------------------------
