@@ -34,8 +34,9 @@ L2_FLUSH_BYTES = 256 << 20
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one capture,
 # profiles/k_render_dram_traffic_1m_gaussians_16cams.md): the forward kernel, and the hit-list
-# replay for the adjoint.  Reported only while render.cu is unchanged (hash).
-TRAFFIC = {"render.cu": "d323c8573f3c4390", "fwd_bytes": 5.52e9, "bwd_bytes": 5.22e9}
+# replay for the adjoint.  Reported only while the kernel sources are unchanged (hash).
+KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
+TRAFFIC = {"kernels": None, "fwd_bytes": None, "bwd_bytes": None}
 
 
 def parse():
@@ -49,6 +50,7 @@ def parse():
                    help="small: 1M Gaussians, two 640x416 cameras (for ncu captures)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-train", action="store_true", help="skip the full training-step measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kbuf", type=int, default=None)
@@ -64,9 +66,12 @@ def parse():
     return p.parse_args()
 
 
-def src_hash(name):
-    with open(os.path.join(ROOT, "paper_2501_19196_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def src_hash(names=KERNEL_SOURCES):
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2501_19196_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -412,7 +417,7 @@ def run_ours(args):
     dom_bytes = bwd_bytes if dom == "bwd" else fwd_bytes
     achieved = dom_bytes / (kms[dom] * 1e-3) / 1e9
     traffic = None
-    if TRAFFIC.get("render.cu") == src_hash("render.cu"):
+    if TRAFFIC.get("kernels") == src_hash():
         traffic = TRAFFIC["bwd_bytes" if dom == "bwd" else "fwd_bytes"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "adjoint: k_replay_list + k_render_bwd + k_finalize" if dom == "bwd"
@@ -451,6 +456,41 @@ def run_ours(args):
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                "path": "pinned host params + dL -> device, graph replay, gradients -> pinned host"}
 
+    # --- full training step: activations, rebuild, render, L2 + D-SSIM loss, adjoint, Adam ---
+    train = None
+    if not args.no_train:
+        from paper_2501_19196_gb300 import TrainStep
+        del g_fb, g_f
+        target = outs[0].clone()  # the images of the scene; training starts from perturbed colours
+        gen = torch.Generator(device="cpu").manual_seed(11)
+        rgb0 = (params[4] + 0.2 * torch.randn(params[4].shape, generator=gen).to(dev)).clamp(0, 1)
+        logit = lambda x: torch.log(x / (1 - x))  # noqa: E731
+        ts = TrainStep(params[0], params[1], logit(params[2]), logit(params[3]), rgb0, params=prm, tune=tune_b,
+                       Q_box=wl.Q)
+        ts.renderer.set_cameras(wl.cams)
+        ms_train, _ = timed(lambda: ts.step(target), max(3, args.steps // 2), 2)
+        l0 = float(ts.step(target).item())
+        lt = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            rgb_out = ts.renderer.render(None, prm)[0]
+            e0.record(stream)
+            ts.loss_fn(rgb_out, target, ts.renderer._cams)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lt.append(e0.elapsed_time(e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        from paper_2501_19196_gb300 import adam_step
+        adam_step(ts.flat, ts.grad, ts.m, ts.v, 1, 0.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.close()
+        train = {"mrays_s": P / ms_train / 1e3 * world, "ms_per_step": ms_train, "loss_ms": sum(lt) / len(lt),
+                 "adam_ms": e0.elapsed_time(e1), "loss_after_warmup": l0, "lambda": 0.2,
+                 "step": "sigmoid activations + LBVH rebuild + render + L2/D-SSIM loss and gradient + adjoint + "
+                         "sigmoid adjoints + Adam (eager launches)"}
+
     # --- CPU oracle baseline (rank 0) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -479,7 +519,7 @@ def run_ours(args):
         "plain": plain,
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
         "kernel_ms": kms,
-        "adjoint_without_hit_lists": replay,
+        "adjoint_without_hit_lists": replay, "training_step": train,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }

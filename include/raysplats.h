@@ -85,8 +85,11 @@ typedef struct {
  *   t_near      smallest accepted entry parameter t1, >= 0 (units of the unit-length ray)
  *   background  added as T_final * background
  *   k_max       at most k_max composited hits per ray, >= 1 (INT32_MAX = unbounded)
- *   depth_mode  0: depth = sum_i w_i t1_i (unnormalised); other values unsupported
- *   sort_key    0: order hits by (t1, id); other values unsupported */
+ *   depth_mode  0: depth = sum_i w_i t_i (unnormalised), t_i the hit's sort key; other
+ *               values unsupported
+ *   sort_key    0: order hits by (t1, id), t1 the ellipsoid entry (Prop. 1); 1: by (t_m, id),
+ *               t_m the ray parameter of the Gaussian's maximum response (Prop. 2, the chord
+ *               midpoint); the hit test (D^2 <= Q, t1 >= t_near) is the same for both */
 typedef struct {
     float Q;
     float eps1;
@@ -105,10 +108,13 @@ typedef struct {
     float* depth;
 } rs_frame;
 
-/* Upstream gradient (device, same layout as rs_frame): d_rgb required, d_alpha may be NULL. */
+/* Upstream gradient (device, same layout as rs_frame): d_rgb required, d_alpha and d_depth
+ * may be NULL.  The depth gradient moves opacities (through alpha) and the hits' sort keys
+ * (through the geometry): the exact derivative of sum_i w_i t_i. */
 typedef struct {
     const float* d_rgb;
     const float* d_alpha;
+    const float* d_depth;
 } rs_frame_grad;
 
 /* Parameter gradients (device, same layout as rs_gaussians).  ACCUMULATED into (+=); the
@@ -172,8 +178,9 @@ typedef struct {
     uint64_t hits_listed;      /* adjoint only: hits replayed from the hit list */
     uint64_t warp_node_fetches;    /* packet traversals: nodes fetched by whole warps; lane
                                       efficiency = nodes_visited / (32 * warp_node_fetches) */
-    uint64_t warp_leaf_iterations; /* packet traversals: leaf-loop iterations of whole warps;
-                                      lane efficiency = gaussians_tested / (32 * this) */
+    uint64_t warp_leaf_iterations; /* packet traversals: full-test iterations of whole warps
+                                      (one per leaf Gaussian whose bounding sphere some lane's
+                                      ray meets); lane efficiency = gaussians_tested / (32 * this) */
 } rs_render_stats;
 
 /* ABI version (RS_ABI_VERSION of the build). */
@@ -303,6 +310,42 @@ rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays,
 rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o,
                         const float* ray_d, const int32_t* sorted_j, float Q, float t_near,
                         float* out, void* cuda_stream);
+
+/* ---- Training-step pieces around the path (Sec. 3 "Loss Function", App. A.7, Sec. 5) ------ */
+
+typedef struct rs_loss_state rs_loss_state;
+
+/* Loss of a batch of rendered images against their targets and its gradient.  For each image
+ * and colour channel, L_ch = (1 - lambda) mean((I - I^)^2) + lambda (1 - SSIM) / 2, with SSIM
+ * the mean over pixels of App. A.7's per-pixel index: an 11 x 11 Gaussian window (sigma 1.5,
+ * normalised), c1 = 0.01^2, c2 = 0.03^2, pixels outside the image taken as 0.  The image loss
+ * is the mean over its three channels (App. A.7) and the batch loss the mean over images.
+ *   rgb, target  device float[P * 3] in the rs_render layout (images concatenated camera by
+ *                camera, pixel-major); only cams[c].width / height are read
+ *   lambda       in [0, 1]
+ *   loss_device  device float: the batch loss (written)
+ *   d_rgb        device float[P * 3]: dL/drgb (written, not accumulated), App. A.7's
+ *                ((E*w) + I^ (F*w) - I (G*w)) form; feed it to rs_render_backward
+ *   *inout       scratch handle (NULL to create, else reused; 36 B per pixel)
+ * Deterministic: the partial sums are reduced in a fixed order. */
+rs_status rs_loss_l2_dssim(const float* rgb, const float* target, const rs_camera* cams,
+                           int32_t n_cams, float lambda, float* loss_device, float* d_rgb,
+                           rs_loss_state** inout, void* cuda_stream);
+rs_status rs_loss_state_destroy(rs_loss_state* state);
+
+/* One Adam update (Sec. 5; the paper uses beta1 0.9, beta2 0.999, eps 1e-8) of `count`
+ * parameters, in place: m = b1 m + (1 - b1) g; v = b2 v + (1 - b2) g^2;
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).  params, m, v: device
+ * float[count] (read and written); grads: device float[count]; step >= 1. */
+rs_status rs_adam_step(float* params, const float* grads, float* m, float* v, int64_t count,
+                       float lr, float beta1, float beta2, float eps, int32_t step,
+                       void* cuda_stream);
+
+/* The sigmoid activation of the opacities and scales (Sec. 5) and its adjoint: y = 1/(1 + e^-x);
+ * dx = dy y (1 - y) (written).  Device float[count] each. */
+rs_status rs_sigmoid(const float* x, float* y, int64_t count, void* cuda_stream);
+rs_status rs_sigmoid_backward(const float* y, const float* dy, float* dx, int64_t count,
+                              void* cuda_stream);
 
 /* Allocation-failure injection, for tests of the out-of-memory paths (the paper has no
  * counterpart).  With n > 0 the n-th device allocation the library makes from now on fails

@@ -6,11 +6,15 @@ include/raysplats.h); this package only binds it.  Importing it does not load th
 """
 from . import build, native  # noqa: F401
 
-__all__ = ["build", "native", "Renderer", "RenderParams", "render_gaussians", "debug_rays"]
+__all__ = ["build", "native", "Renderer", "RenderParams", "render_gaussians", "debug_rays", "ImageLoss",
+           "TrainStep", "adam_step", "sigmoid", "sigmoid_backward"]
 
 
 def __getattr__(name):
     if name in ("Renderer", "RenderParams", "render_gaussians", "debug_rays"):
         from . import renderer
         return getattr(renderer, name)
+    if name in ("ImageLoss", "TrainStep", "adam_step", "sigmoid", "sigmoid_backward"):
+        from . import train
+        return getattr(train, name)
     raise AttributeError(name)

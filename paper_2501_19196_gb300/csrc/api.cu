@@ -40,20 +40,28 @@ static bool injected_alloc_failure() {
     return --g_fail_alloc_in == 0;
 }
 
+rs_status device_realloc(void** p, size_t bytes) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (injected_alloc_failure())
+        return set_error(RS_ERR_OOM, "injected allocation failure (rs_test_fail_alloc) of %lld bytes",
+                         (long long)bytes);
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(RS_ERR_OOM, "cudaMalloc of %lld bytes failed", (long long)bytes);
+    }
+    return RS_OK;
+}
+
 // (re)allocate a device buffer of `count` elements, freeing the previous one
 template <typename T>
 static rs_status dmalloc(T*& p, int64_t count) {
-    if (p) cudaFree(p);
-    p = nullptr;
-    if (count <= 0) count = 1;
-    if (injected_alloc_failure())
-        return set_error(RS_ERR_OOM, "injected allocation failure (rs_test_fail_alloc) of %lld bytes",
-                         (long long)(sizeof(T) * count));
-    if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(T) * (size_t)count) != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(RS_ERR_OOM, "cudaMalloc of %lld bytes failed", (long long)(sizeof(T) * count));
-    }
-    return RS_OK;
+    void* q = p;
+    const rs_status st = device_realloc(&q, sizeof(T) * (size_t)(count > 0 ? count : 1));
+    p = static_cast<T*>(q);
+    return st;
 }
 
 static int sm_count() {
@@ -201,8 +209,9 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     if (!(p->eps1 >= 0.f) || !finite(p->eps1) || !(p->t_near >= 0.f) || !finite(p->t_near))
         return set_error(RS_ERR_INVALID_ARG, "eps1 and t_near must be finite and >= 0");
     if (p->k_max < 1) return set_error(RS_ERR_INVALID_ARG, "k_max must be >= 1");
-    if (p->depth_mode != 0 || p->sort_key != 0)
-        return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 and sort_key 0 are implemented");
+    if (p->depth_mode != 0) return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 is implemented");
+    if (p->sort_key != 0 && p->sort_key != 1)
+        return set_error(RS_ERR_INVALID_ARG, "sort_key %d: must be 0 (entry t1) or 1 (t_m)", p->sort_key);
     for (int k = 0; k < 3; ++k)
         if (!finite(p->background[k])) return set_error(RS_ERR_INVALID_ARG, "background must be finite");
     if (!out || !out->rgb || !out->alpha) return set_error(RS_ERR_INVALID_ARG, "output rgb/alpha are NULL");
@@ -313,6 +322,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     P.n_gauss = (int32_t)g->n;
     P.n_nodes = (int32_t)std::max<int64_t>(1, g->n - 1);
     P.list_cap = tune->hit_list;
+    P.sort_key = p->sort_key;
     P.ids = tune->hit_list > 0 ? S->ids : nullptr;
     S->P = P;
 
@@ -343,7 +353,7 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         A.total_tiles = tiles;
         if (cudaMemsetAsync(S->queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return cuda_check("queue reset");
         const int grid = (int)std::min<int64_t>(
-            persistent_grid(false, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
+            persistent_grid_fwd(tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
             (tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_forward(A, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                              block, s);
@@ -427,7 +437,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
     A.err = accel->err;
     A.stats = reinterpret_cast<unsigned long long*>(stats);
     const bool count = stats != nullptr;
-    BwdArgs B{dl->d_rgb, dl->d_alpha, S->gtmp, list ? S->ovf : nullptr, list ? S->cap_ovf : 0};
+    BwdArgs B{dl->d_rgb, dl->d_alpha, dl->d_depth, S->gtmp, list ? S->ovf : nullptr, list ? S->cap_ovf : 0};
     const int block = 32 * tune->block_warps;
     if (cudaMemsetAsync(S->queue + 1, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess)
         return cuda_check("queue reset");
@@ -436,7 +446,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         if (tune->persistent) {
             A.cam_single = -1;
             A.total_tiles = S->total_tiles;
-            const int grid = (int)std::min<int64_t>(list_replay_grid(count, block, sm_count()),
+            const int grid = (int)std::min<int64_t>(list_replay_grid(count, block, sm_count(), dl->d_depth != nullptr),
                                                     (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
             const cudaError_t e = launch_list_replay(A, B, true, count, std::max(grid, 1), block, s);
             if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "list replay launch: %s", cudaGetErrorString(e));
@@ -454,7 +464,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         A.cam_single = -1;
         A.total_tiles = S->total_tiles;
         const int grid = (int)std::min<int64_t>(
-            persistent_grid(true, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
+            persistent_grid_bwd(tune->kbuf, block, count, tune->traversal, A.n_top, sm_count(), dl->d_depth != nullptr),
             (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                               block, s);
@@ -463,7 +473,7 @@ static rs_status backward_impl(const rs_gaussians* g, const rs_accel* accel, con
         A.cam_single = -1;
         A.total_tiles = S->total_tiles;
         const int grid = (int)std::min<int64_t>(
-            persistent_grid(true, tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
+            persistent_grid_bwd(tune->kbuf, block, count, tune->traversal, A.n_top, sm_count(), dl->d_depth != nullptr),
             (S->total_tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_backward(A, B, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                               block, s);

@@ -116,8 +116,8 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     if (!(p->Q > 0.f) || !std::isfinite(p->Q) || !(p->eps1 >= 0.f) || !std::isfinite(p->eps1) ||
         !(p->t_near >= 0.f) || !std::isfinite(p->t_near) || p->k_max < 1)
         return set_error(RS_ERR_INVALID_ARG, "bad render parameters");
-    if (p->depth_mode != 0 || p->sort_key != 0)
-        return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 and sort_key 0 are implemented");
+    if (p->depth_mode != 0) return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 is implemented");
+    if (p->sort_key != 0 && p->sort_key != 1) return set_error(RS_ERR_INVALID_ARG, "sort_key must be 0 or 1");
     DevCam table[kCams];
     int64_t tiles = 0, pix = 0;
     for (int c = 0; c < n_cams; ++c) {
@@ -208,6 +208,7 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     F.P.n_nodes = (int32_t)std::max<int64_t>(1, g->n - 1);
     F.P.list_cap = 0;  // forward only: no hit list
     F.P.ids = nullptr;
+    F.P.sort_key = p->sort_key;
     F.rgb = out->rgb;
     F.alpha = out->alpha;
     F.depth = out->depth;
@@ -221,7 +222,7 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int block = 32 * tune->block_warps;
-    const int grid = (int)std::min<int64_t>(persistent_grid(false, tune->kbuf, block, false, tune->traversal, F.n_top, sms),
+    const int grid = (int)std::min<int64_t>(persistent_grid_fwd(tune->kbuf, block, false, tune->traversal, F.n_top, sms),
                                             (tiles + tune->block_warps - 1) / tune->block_warps);
     const cudaError_t e = launch_forward(F, tune->kbuf, true, false, tune->traversal, std::max(grid, 1), block, s);
     if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "fixed scratch render launch: %s", cudaGetErrorString(e));

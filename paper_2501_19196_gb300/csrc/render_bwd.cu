@@ -1,0 +1,317 @@
+// render_bwd.cu -- the adjoint kernels (a10): hit-list replay, re-traversal of the overflow
+// tiles, and the finalize map to (quaternion, scale); plus their launchers.
+#include <algorithm>
+
+#include "trace.cuh"
+
+namespace rs {
+
+// List replay (adjoint, first launch): one warp per ray tile of the forward pass; every ray
+// whose hits all fit in its hit list is replayed from it (replay_list).  A tile holding a ray
+// with more hits is appended to the overflow list, which k_render_bwd re-traverses next.
+template <bool PERSIST, bool COUNT, bool DEPTH>
+__global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
+    const int lane = threadIdx.x & 31;
+    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Counters cnt;
+    uint32_t rays = 0;
+    uint64_t listed = 0;
+    while (true) {
+        if (PERSIST) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(A.queue + 1, 1ull);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (tile >= A.total_tiles) break;
+        DevCam cam;
+        int px, py;
+        int64_t pix;
+        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
+        const int n = valid ? A.sn[pix] : 0;
+        const int nl = n <= A.P.list_cap ? n : 0;
+        float3 o, d;
+        camera_ray(cam, px, py, o, d);
+        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f};
+        float Tf = 1.f;
+        if (nl > 0) {
+            g.c[0] = B.d_rgb[3 * pix];
+            g.c[1] = B.d_rgb[3 * pix + 1];
+            g.c[2] = B.d_rgb[3 * pix + 2];
+            g.a = B.d_alpha ? B.d_alpha[pix] : 0.f;
+            g.d = DEPTH ? B.d_depth[pix] : 0.f;
+            Tf = A.sT[pix];
+        }
+        if (COUNT && n > 0) ++rays;
+        if (COUNT) listed += nl;
+        replay_list<COUNT, DEPTH>(A.rec, A.P, pix, o, d, Tf, nl, g, B.gtmp, cnt, A.err);
+        if (__any_sync(0xffffffffu, n > A.P.list_cap) && lane == 0) {
+            const int64_t global = A.cam_single < 0 ? tile : A.cams[A.cam_single].tile_base + tile;
+            const unsigned long long slot = atomicAdd(A.queue + 3, 1ull);
+            if (slot < (unsigned long long)B.ovf_cap) B.ovf[slot] = (int)global;
+            else atomicOr(A.err, kErrIndex);
+        }
+        if (!PERSIST) break;
+    }
+    if (COUNT) {
+        unsigned long long v[kNumStats] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kNumStats; ++k)
+                if (v[k]) atomicAdd(A.stats + k, v[k]);
+        }
+    }
+}
+
+template <int K, bool PERSIST, bool COUNT, int MODE, bool DEPTH>
+__global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
+    extern __shared__ float4 s_top[];
+    if (B.ovf && A.queue[3] == 0) return;  // every ray was replayed from its hit list
+    if (MODE != 3)
+        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
+    __syncthreads();
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
+                     A.P.n_gauss, A.err};
+    const int lane = threadIdx.x & 31;
+    // with a hit list, only the tiles the list replay found overflowing are re-traversed
+    const int64_t n_tiles = B.ovf ? (int64_t)min((unsigned long long)B.ovf_cap, A.queue[3]) : A.total_tiles;
+    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    Counters cnt;
+    uint32_t rays = 0, retraced = 0;
+    while (true) {
+        if (PERSIST) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(A.queue + 2, 1ull);
+            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        }
+        if (tile >= n_tiles) break;
+        if (B.ovf) tile = B.ovf[tile];
+        DevCam cam;
+        int px, py;
+        int64_t pix;
+        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
+        const int n = valid ? A.sn[pix] : 0;
+        const int nt = n > A.P.list_cap ? n : 0;  // rays the hit list cannot replay
+        float3 o, d;
+        camera_ray(cam, px, py, o, d);
+        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f};
+        float Tf = 1.f;
+        int64_t lk = -1;
+        if (nt > 0) {
+            g.c[0] = B.d_rgb[3 * pix];
+            g.c[1] = B.d_rgb[3 * pix + 1];
+            g.c[2] = B.d_rgb[3 * pix + 2];
+            g.a = B.d_alpha ? B.d_alpha[pix] : 0.f;
+            g.d = DEPTH ? B.d_depth[pix] : 0.f;
+            Tf = A.sT[pix];
+            lk = A.skey[pix];
+            if (COUNT) {
+                ++retraced;
+                if (A.P.list_cap == 0) ++rays;
+            }
+        }
+        if (MODE == 3)
+            trace_backward_bf<K, COUNT, 4, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
+        else if (MODE == 2)
+            trace_backward_bf<K, COUNT, 2, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
+        else if (MODE == 1)
+            trace_backward_packet<K, COUNT, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
+        else if (nt > 0)
+            trace_backward<K, COUNT, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
+        if (!PERSIST) break;
+    }
+    if (COUNT) {
+        unsigned long long v[kNumStats] = {rays,     cnt.nodes, cnt.tests, cnt.hits,   cnt.rounds,
+                                           cnt.inserted, retraced, 0,        cnt.wnodes, cnt.wleaf};
+#pragma unroll
+        for (int k = 0; k < kNumStats; ++k) {
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < kNumStats; ++k) atomicAdd(A.stats + k, v[k]);
+        }
+    }
+}
+
+// dL/dM, dL/dm, dL/dopacity, dL/drgb (Morton order) -> caller's gradients (Gaussian ids).
+// M = S^-1 R^T:  dL/ds_k = -(1/s_k) sum_l G[k][l] M[k][l];  dL/dR[l][k] = G[k][l] / s_k;
+// R = I + s_q K(q), s_q = 2/|q|^2 (App. A.6):  dR/dq_x = -s_q^2 q_x K + s_q dK/dq_x.
+__global__ void k_finalize(const float4* __restrict__ gtmp, const float4* __restrict__ rec,
+                           const uint32_t* __restrict__ perm, const float* __restrict__ quats,
+                           const float* __restrict__ scales, int64_t n, rs_gaussian_grads out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i = perm[j];
+    const float4 G0 = gtmp[4 * j], G1 = gtmp[4 * j + 1], G2 = gtmp[4 * j + 2], G3 = gtmp[4 * j + 3];
+    if (out.d_means) {
+        out.d_means[3 * i] += G0.w;
+        out.d_means[3 * i + 1] += G1.w;
+        out.d_means[3 * i + 2] += G2.w;
+    }
+    if (out.d_opacities) out.d_opacities[i] += G3.x;
+    if (out.d_rgb) {
+        out.d_rgb[3 * i] += G3.y;
+        out.d_rgb[3 * i + 1] += G3.z;
+        out.d_rgb[3 * i + 2] += G3.w;
+    }
+    if (!out.d_scales && !out.d_quats) return;
+    const float GM[3][3] = {{G0.x, G0.y, G0.z}, {G1.x, G1.y, G1.z}, {G2.x, G2.y, G2.z}};
+    const float4 m0 = rec[4 * j], m1 = rec[4 * j + 1], m2 = rec[4 * j + 2];
+    const float M[3][3] = {{m0.x, m0.y, m0.z}, {m1.x, m1.y, m1.z}, {m2.x, m2.y, m2.z}};
+    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+    if (out.d_scales) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            out.d_scales[3 * i + k] += -(GM[k][0] * M[k][0] + GM[k][1] * M[k][1] + GM[k][2] * M[k][2]) / s[k];
+    }
+    if (out.d_quats) {
+        const float qa = quats[4 * i], qb = quats[4 * i + 1], qc = quats[4 * i + 2], qd = quats[4 * i + 3];
+        const float sq = 2.f / (qa * qa + qb * qb + qc * qc + qd * qd);
+        float GR[3][3];  // dL/dR[l][k]
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) GR[l][k] = GM[k][l] / s[k];
+        const float Kq[3][3] = {{-(qc * qc + qd * qd), qb * qc - qa * qd, qb * qd + qa * qc},
+                                {qb * qc + qa * qd, -(qb * qb + qd * qd), qc * qd - qa * qb},
+                                {qb * qd - qa * qc, qc * qd + qa * qb, -(qb * qb + qc * qc)}};
+        float GK = 0.f;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) GK += GR[l][k] * Kq[l][k];
+        // sum over entries of GR (.) dK/dq_x
+        const float da = GR[0][1] * (-qd) + GR[0][2] * qc + GR[1][0] * qd + GR[1][2] * (-qb) + GR[2][0] * (-qc) +
+                         GR[2][1] * qb;
+        const float db = GR[0][1] * qc + GR[0][2] * qd + GR[1][0] * qc + GR[1][1] * (-2.f * qb) + GR[1][2] * (-qa) +
+                         GR[2][0] * qd + GR[2][1] * qa + GR[2][2] * (-2.f * qb);
+        const float dc = GR[0][0] * (-2.f * qc) + GR[0][1] * qb + GR[0][2] * qa + GR[1][0] * qb + GR[1][2] * qd +
+                         GR[2][0] * (-qa) + GR[2][1] * qd + GR[2][2] * (-2.f * qc);
+        const float dd = GR[0][0] * (-2.f * qd) + GR[0][1] * (-qa) + GR[0][2] * qb + GR[1][0] * qa +
+                         GR[1][1] * (-2.f * qd) + GR[1][2] * qc + GR[2][0] * qb + GR[2][1] * qc;
+        const float ns = -sq * sq * GK;
+        out.d_quats[4 * i] += ns * qa + sq * da;
+        out.d_quats[4 * i + 1] += ns * qb + sq * db;
+        out.d_quats[4 * i + 2] += ns * qc + sq * dc;
+        out.d_quats[4 * i + 3] += ns * qd + sq * dd;
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------------
+static size_t smem_bytes(int n_top) { return (size_t)n_top * 4 * sizeof(float4); }
+
+template <int K, bool COUNT, int MODE, bool DEPTH>
+static int occupancy_bwd(int block, size_t smem) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, true, COUNT, MODE, DEPTH>, block, smem);
+    return nb;
+}
+
+template <int K, bool COUNT, bool DEPTH>
+static int occupancy_bwd_m(int block, int mode, size_t smem) {
+    if (mode == 3) return occupancy_bwd<K, COUNT, 3, DEPTH>(block, 0);
+    if (mode == 2) return occupancy_bwd<K, COUNT, 2, DEPTH>(block, smem);
+    if (mode == 1) return occupancy_bwd<K, COUNT, 1, DEPTH>(block, smem);
+    return occupancy_bwd<K, COUNT, 0, DEPTH>(block, smem);
+}
+
+template <int K, bool DEPTH>
+static int occupancy_bwd_k(int block, bool count, int mode, size_t smem) {
+    return count ? occupancy_bwd_m<K, true, DEPTH>(block, mode, smem) : occupancy_bwd_m<K, false, DEPTH>(block, mode, smem);
+}
+
+int persistent_grid_bwd(int K, int block, bool count, int mode, int n_top, int sms, bool depth) {
+    const size_t sm = smem_bytes(n_top);
+    int nb = 1;
+    if (K == 8) nb = depth ? occupancy_bwd_k<8, true>(block, count, mode, sm) : occupancy_bwd_k<8, false>(block, count, mode, sm);
+    else if (K == 16)
+        nb = depth ? occupancy_bwd_k<16, true>(block, count, mode, sm) : occupancy_bwd_k<16, false>(block, count, mode, sm);
+    else nb = depth ? occupancy_bwd_k<32, true>(block, count, mode, sm) : occupancy_bwd_k<32, false>(block, count, mode, sm);
+    return std::max(1, nb) * sms;
+}
+
+template <int K, bool PERSIST, bool COUNT, bool DEPTH>
+static void launch_bwd_mode(const FwdArgs& A, const BwdArgs& B, int mode, int grid, int block, cudaStream_t st) {
+    const size_t sm = smem_bytes(A.n_top);
+    if (mode == 3) k_render_bwd<K, PERSIST, COUNT, 3, DEPTH><<<grid, block, 0, st>>>(A, B);
+    else if (mode == 2) k_render_bwd<K, PERSIST, COUNT, 2, DEPTH><<<grid, block, sm, st>>>(A, B);
+    else if (mode == 1) k_render_bwd<K, PERSIST, COUNT, 1, DEPTH><<<grid, block, sm, st>>>(A, B);
+    else k_render_bwd<K, PERSIST, COUNT, 0, DEPTH><<<grid, block, sm, st>>>(A, B);
+}
+
+template <int K, bool DEPTH>
+static void launch_bwd_k(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int mode, int grid, int block,
+                         cudaStream_t st) {
+    if (persistent) {
+        if (count) launch_bwd_mode<K, true, true, DEPTH>(A, B, mode, grid, block, st);
+        else launch_bwd_mode<K, true, false, DEPTH>(A, B, mode, grid, block, st);
+    } else {
+        if (count) launch_bwd_mode<K, false, true, DEPTH>(A, B, mode, grid, block, st);
+        else launch_bwd_mode<K, false, false, DEPTH>(A, B, mode, grid, block, st);
+    }
+}
+
+template <bool DEPTH>
+static cudaError_t launch_bwd_d(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
+                                int grid, int block, cudaStream_t st) {
+    if (K == 8) launch_bwd_k<8, DEPTH>(A, B, persistent, count, mode, grid, block, st);
+    else if (K == 16) launch_bwd_k<16, DEPTH>(A, B, persistent, count, mode, grid, block, st);
+    else if (K == 32) launch_bwd_k<32, DEPTH>(A, B, persistent, count, mode, grid, block, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
+                            int grid, int block, cudaStream_t st) {
+    return B.d_depth ? launch_bwd_d<true>(A, B, K, persistent, count, mode, grid, block, st)
+                     : launch_bwd_d<false>(A, B, K, persistent, count, mode, grid, block, st);
+}
+
+template <bool PERSIST, bool COUNT, bool DEPTH>
+static int list_occupancy(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_replay_list<PERSIST, COUNT, DEPTH>, block, 0);
+    return nb;
+}
+
+int list_replay_grid(bool count, int block, int sms, bool depth) {
+    const int nb = depth ? (count ? list_occupancy<true, true, true>(block) : list_occupancy<true, false, true>(block))
+                         : (count ? list_occupancy<true, true, false>(block) : list_occupancy<true, false, false>(block));
+    return std::max(1, nb) * sms;
+}
+
+template <bool DEPTH>
+static void launch_list_d(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
+                          cudaStream_t st) {
+    if (persistent) {
+        if (count) k_replay_list<true, true, DEPTH><<<grid, block, 0, st>>>(A, B);
+        else k_replay_list<true, false, DEPTH><<<grid, block, 0, st>>>(A, B);
+    } else {
+        if (count) k_replay_list<false, true, DEPTH><<<grid, block, 0, st>>>(A, B);
+        else k_replay_list<false, false, DEPTH><<<grid, block, 0, st>>>(A, B);
+    }
+}
+
+cudaError_t launch_list_replay(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
+                               cudaStream_t st) {
+    if (B.d_depth) launch_list_d<true>(A, B, persistent, count, grid, block, st);
+    else launch_list_d<false>(A, B, persistent, count, grid, block, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,
+                            const float* scales, int64_t n, const rs_gaussian_grads& out, cudaStream_t st) {
+    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gtmp, rec, perm, quats, scales, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rs

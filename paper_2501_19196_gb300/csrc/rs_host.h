@@ -52,4 +52,9 @@ rs_status cuda_check(const char* what);
 
 rs_status build_accel_device(Accel& A, const rs_gaussians& g, const rs_tune_params& tp, cudaStream_t st);
 
+// Free *p (if any) and allocate `bytes` of device memory into it (at least 1 byte).  Honours
+// the allocation-failure injection of rs_test_fail_alloc; on failure *p is NULL and RS_ERR_OOM
+// is returned with a message.
+rs_status device_realloc(void** p, size_t bytes);
+
 }  // namespace rs

@@ -59,6 +59,7 @@ struct TraceParams {
     int32_t n_nodes;       // guard: node references lie in [0, n_nodes) (or the staged slots)
     int32_t list_cap;      // hit list: ids of the first list_cap composited hits per ray (0: none)
     int* ids;              // hit list storage, list_cap ints per pixel (pixel-major rows)
+    int32_t sort_key;      // hits ordered by 0: entry t1, 1: t_m (maximum response)
 };
 
 // (t1, sorted id) packed into one ordered 64-bit key; t1 >= 0 so its bit pattern orders as
@@ -102,6 +103,7 @@ __device__ __forceinline__ void camera_ray(const DevCam& c, int px, int py, floa
 // ---------------------------------------------------------------------------------------------
 struct Hit {
     float D2, t1;
+    float tm;    // ray parameter of the maximum response (chord midpoint)
     bool hit;
     float p[3];  // M-space closest-approach vector
     float v[3];  // world vector from the mean to the point of maximum response
@@ -146,6 +148,7 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
     const float a = __fmaf_rn(dp[2], dp[2], __fmaf_rn(dp[1], dp[1], __fmul_rn(dp[0], dp[0])));
     const float b = __fmaf_rn(op[2], dp[2], __fmaf_rn(op[1], dp[1], __fmul_rn(op[0], dp[0])));
     const float tm = -__fdiv_rn(b, a);
+    h.tm = __fadd_rn(tc, tm);
     float p[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] = __fmaf_rn(tm, dp[k], op[k]);
@@ -174,6 +177,12 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
             h.v[k] = __fmaf_rn(tm, dd[k], w[k]);
         }
     }
+}
+
+// The ordering parameter of a hit: its entry t1, or (sort key 1) the parameter of the maximum
+// response, which is never below t1 (the max guards FP32 rounding at grazing incidence).
+__device__ __forceinline__ float hit_key_t(const Hit& h, int sort_key) {
+    return sort_key ? fmaxf(h.tm, h.t1) : h.t1;
 }
 
 // alpha_i = opacity * exp(-D2 / 2)  (Eq. 8, Prop. 2)

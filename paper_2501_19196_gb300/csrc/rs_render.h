@@ -38,14 +38,16 @@ struct FwdArgs {
 struct BwdArgs {
     const float* d_rgb;
     const float* d_alpha;
+    const float* d_depth;  // may be NULL
     float4* gtmp;  // 4 per Gaussian (Morton order): (dM row k, dm_k) k = 0..2, (dop, drgb)
     int* ovf;      // tiles (global ids) holding a ray with more hits than its hit list; NULL:
                    // the re-traversing adjoint covers every tile
     int64_t ovf_cap;
 };
 
-int persistent_grid(bool backward, int K, int block, bool count, int mode, int n_top, int sms);
-int list_replay_grid(bool count, int block, int sms);
+int persistent_grid_fwd(int K, int block, bool count, int mode, int n_top, int sms);
+int persistent_grid_bwd(int K, int block, bool count, int mode, int n_top, int sms, bool depth);
+int list_replay_grid(bool count, int block, int sms, bool depth);
 cudaError_t launch_list_replay(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
                                cudaStream_t st);
 cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,

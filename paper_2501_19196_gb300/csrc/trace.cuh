@@ -1,4 +1,6 @@
-// render.cu -- per-ray traversal, compositing and the adjoint (RaySplats, arXiv 2501.19196).
+// trace.cuh -- the device side of the rendering path shared by the forward and adjoint kernels
+// (render_fwd.cu, render_bwd.cu): ray/box and ray/ellipsoid tests, k-buffers, the warp
+// node queue, the per-ray and warp-packet traversals, and the per-hit adjoint.
 //
 // Forward (a7-a9): each lane traces one camera ray.  A round traverses the LBVH with a
 // register k-buffer of the K nearest hits whose (t1, id) key lies beyond the last composited
@@ -19,6 +21,8 @@
 //
 // Launch modes: plain (one launch per camera, one warp per 32-ray tile) and persistent (one
 // launch over every camera's tiles, warps pull tiles from a device counter).
+#pragma once
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,9 +60,30 @@ struct NodeSrc {
 
 // a leaf's Gaussian count after the range check (a corrupt range reads nothing and is reported)
 __device__ __forceinline__ int leaf_count(const NodeSrc& ns, int start, int cnt) {
-    if (start >= 0 && cnt >= 0 && start <= ns.n_gauss - cnt) return cnt;
+    if (start >= 0 && cnt >= 0 && cnt <= 32 && start <= ns.n_gauss - cnt) return cnt;
     atomicOr(ns.err, kErrIndex);
     return 0;
+}
+
+// Bounding-sphere pre-test of one leaf for the whole warp: the leaf's spheres are loaded once
+// (lane i holds Gaussian start + i) and broadcast by shuffles.  Bit g of the result is set when
+// this lane wants the leaf and its ray may hit Gaussian start + g.  num <= 32 (leaf_size <= 16).
+__device__ __forceinline__ uint32_t leaf_sphere_mask(const float4* __restrict__ sph, int start, int num, bool want,
+                                                     const float3 o, const float3 d) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float4 mine = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (lane < num) mine = __ldg(sph + start + lane);
+    uint32_t mask = 0;
+    for (int g = 0; g < num; ++g) {
+        float4 sp;
+        sp.x = __shfl_sync(FULL, mine.x, g);
+        sp.y = __shfl_sync(FULL, mine.y, g);
+        sp.z = __shfl_sync(FULL, mine.z, g);
+        sp.w = __shfl_sync(FULL, mine.w, g);
+        if (want && sphere_may_hit(o, d, sp)) mask |= 1u << g;
+    }
+    return mask;
 }
 
 // The children of one node as seen by the traversal: W = 2 reads a binary node (possibly staged
@@ -203,10 +228,161 @@ __device__ __forceinline__ void kbuf_pop_front(int64_t (&keys)[K], int64_t empty
     keys[K - 1] = empty;
 }
 
+// Occupancy-aware variants for warp-converged callers.  A lane's buffer holds nk keys in slots
+// [0, nk); the rest are empty.  The warp sizes the compare-exchange network by the largest nk
+// among the lanes taking part (a uniform choice), so a sparsely filled buffer costs a short
+// network instead of all K stages.  Results equal those of the full-width functions above.
+template <int K, int C, bool DESC>
+__device__ __forceinline__ void kbuf_insert_at(int64_t (&keys)[K], int64_t key) {
+    keys[C] = key;  // free for every inserting lane (nk <= C), or the dropped last slot (C = K-1)
+#pragma unroll
+    for (int s = C; s > 0; --s) {
+        const int64_t ka = keys[s - 1], kb = keys[s];
+        keys[s - 1] = DESC ? max(ka, kb) : min(ka, kb);
+        keys[s] = DESC ? min(ka, kb) : max(ka, kb);
+    }
+}
+
+// insert `key` where `ins` (all 32 lanes call); a full buffer drops its last key.  DESC: the
+// descending buffer of the adjoint.
+template <int K, bool DESC = false>
+__device__ __forceinline__ void kbuf_insert_warp(int64_t (&keys)[K], int& nk, bool ins, int64_t key) {
+    const int m = (int)__reduce_max_sync(0xffffffffu, ins ? (unsigned)nk : 0u);
+    if constexpr (K > 8) {
+        if (m < 8) {
+            if (ins) kbuf_insert_at<K, 8, DESC>(keys, key);
+            if (ins) ++nk;
+            return;
+        }
+    }
+    if constexpr (K > 16) {
+        if (m < 16) {
+            if (ins) kbuf_insert_at<K, 16, DESC>(keys, key);
+            if (ins) ++nk;
+            return;
+        }
+    }
+    if constexpr (K > 24) {
+        if (m < 24) {
+            if (ins) kbuf_insert_at<K, 24, DESC>(keys, key);
+            if (ins) ++nk;
+            return;
+        }
+    }
+    if (ins) {
+        kbuf_insert_at<K, K - 1, DESC>(keys, key);
+        if (nk < K) ++nk;
+    }
+}
+
+template <int K, int C>
+__device__ __forceinline__ void kbuf_pop_upto(int64_t (&keys)[K], int64_t empty) {
+#pragma unroll
+    for (int s = 0; s < C; ++s) keys[s] = keys[s + 1];
+    keys[C] = empty;
+}
+
+// drop keys[0] in the lanes of `group` (the calling lanes, converged)
+template <int K>
+__device__ __forceinline__ void kbuf_pop_warp(int64_t (&keys)[K], int& nk, int64_t empty, unsigned group) {
+    const int m = (int)__reduce_max_sync(group, (unsigned)nk);
+    --nk;
+    if constexpr (K > 8) {
+        if (m <= 8) {
+            kbuf_pop_upto<K, 8>(keys, empty);
+            return;
+        }
+    }
+    kbuf_pop_front<K>(keys, empty);
+}
+
 struct Counters {
     uint32_t nodes = 0, tests = 0, hits = 0, rounds = 0, inserted = 0;
     uint32_t wnodes = 0, wleaf = 0;  // packet modes: node fetches and leaf iterations of whole warps
 };
+
+// Running state of one ray's back-to-front replay: the transmittance in front of the next hit
+// to replay and the colour / alpha / depth composited behind it (App. A.4-A.5).
+struct Adjoint {
+    float Tn, U0, U1, U2, UA, UD;
+};
+
+// Upstream gradient of one ray: dL/d(rgb), dL/d(alpha), dL/d(depth).
+struct Upstream {
+    float c[3], a, d;
+};
+
+// The adjoint of one composited hit (sorted Gaussian j), given the hits behind it: recovers
+// T_i = T_{i+1} / (1 - alpha_i), forms dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) +
+// g_A (1 - U_A) + g_D (t_i - U_D)), advances U, and returns the 16-float contribution
+// (dM rows + dm, dopacity + drgb) in v.  alpha comes from the same solve as in the forward
+// pass, so it has the same bits.  The depth term also moves the hit's key t_i:
+//   t_m = -<o',d'>/a:  dt_m/dM = -(d' v^T + p d^T)/a,  dt_m/dm = M^T d'/a;
+//   t1 = t_m - r, r = sqrt((Q - D2)/a):
+//                      dt1/dM = (-d' v^T - p d^T + p v^T / r + r d' d^T)/a,
+//                      dt1/dm = M^T (d' - p/r)/a,
+// with d' = M d, p = M v and v the closest point minus the mean.
+template <bool DEPTH>
+__device__ __forceinline__ void adjoint_hit(const float4* __restrict__ rec, int j, const float3 o, const float3 d,
+                                            const TraceParams& P, Adjoint& s, const Upstream& g,
+                                            float4 (&v)[4]) {
+    const float4 g0 = __ldg(rec + 4 * j + 0);
+    const float4 g1 = __ldg(rec + 4 * j + 1);
+    const float4 g2 = __ldg(rec + 4 * j + 2);
+    const float4 sh = __ldg(rec + 4 * j + 3);
+    Hit h;
+    ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+    const float tk = DEPTH ? hit_key_t(h, P.sort_key) : 0.f;
+    const float e = expf(__fmul_rn(-0.5f, h.D2));
+    const float a = __fmul_rn(sh.x, e);
+    const float om = __fsub_rn(1.f, a);
+    const float Ti = __fdiv_rn(s.Tn, om);
+    const float w = Ti * a;
+    float dLda = Ti * (g.c[0] * (sh.y - s.U0) + g.c[1] * (sh.z - s.U1) + g.c[2] * (sh.w - s.U2) + g.a * (1.f - s.UA));
+    if (DEPTH) dLda = fmaf(Ti, g.d * (tk - s.UD), dLda);
+    s.U0 = fmaf(a, sh.y, om * s.U0);
+    s.U1 = fmaf(a, sh.z, om * s.U1);
+    s.U2 = fmaf(a, sh.w, om * s.U2);
+    s.UA = fmaf(om, s.UA, a);
+    if (DEPTH) s.UD = fmaf(a, tk, om * s.UD);
+    s.Tn = Ti;
+    const float gD2 = -0.5f * a * dLda;
+    const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
+    const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);  // dL/dm = -M^T (2 gD2 p)
+    const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
+    const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+    v[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
+    v[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
+    v[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
+    v[3] = make_float4(dLda * e, g.c[0] * w, g.c[1] * w, g.c[2] * w);
+    const float gt = DEPTH ? g.d * w : 0.f;  // dL/dt_i: depth = sum w_i t_i
+    if (DEPTH && gt != 0.f) {
+        const float dd[3] = {d.x, d.y, d.z};
+        const float4 rows[3] = {g0, g1, g2};
+        float dp[3];  // d' = M d
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dp[k] = rows[k].x * d.x + rows[k].y * d.y + rows[k].z * d.z;
+        const float aa = dp[0] * dp[0] + dp[1] * dp[1] + dp[2] * dp[2];
+        const bool t1key = P.sort_key == 0;
+        const float rr = t1key ? sqrtf(fmaxf(P.Q - h.D2, 0.f) / aa) : 0.f;  // half chord
+        const float ir = t1key ? 1.f / fmaxf(rr, 1e-20f) : 0.f;
+        const float ga = gt / aa;
+        float x[3];  // d' - p/r (t1) or d' (t_m): dt/dm = M^T x / a
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = dp[k] - h.p[k] * ir;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // row k of dt/dM: (-d'_k + p_k / r) v^T + (-p_k + r d'_k) d^T
+            const float cv = -dp[k] + h.p[k] * ir, cd = -h.p[k] + rr * dp[k];
+            v[k].x += ga * (cv * h.v[0] + cd * dd[0]);
+            v[k].y += ga * (cv * h.v[1] + cd * dd[1]);
+            v[k].z += ga * (cv * h.v[2] + cd * dd[2]);
+        }
+        v[0].w += ga * (rows[0].x * x[0] + rows[1].x * x[1] + rows[2].x * x[2]);
+        v[1].w += ga * (rows[0].y * x[0] + rows[1].y * x[1] + rows[2].y * x[2]);
+        v[2].w += ga * (rows[0].z * x[0] + rows[1].z * x[1] + rows[2].z * x[2]);
+    }
+}
 
 // ---------------------------------------------------------------------------------------------
 // Forward: one streaming pass per ray.
@@ -312,7 +488,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                         ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                         if (COUNT) cnt.tests++;
                         if (h.hit) {
-                            const int64_t key = pack_key(h.t1, q);
+                            const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
                             if (key > lo_key && key < cap) {
                                 if (key < keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];  // evicted
@@ -396,18 +572,17 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
 // unprocessed hit and is replayed at once, back to front.  Boxes entering beyond the last
 // composited hit are pruned.  Overflow is handled with a key floor and a further pass.
 // ---------------------------------------------------------------------------------------------
-template <int K, bool COUNT>
+template <int K, bool COUNT, bool DEPTH>
 __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                const TraceParams& P, const float3 o, const float3 d, float T_final,
-                                               int64_t last_key, int n_hits, const float gC[3], float gA,
+                                               int64_t last_key, int n_hits, const Upstream& g,
                                                float4* __restrict__ gtmp, Counters& cnt, int* err) {
     if (n_hits <= 0) return;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float NINF = __int_as_float(0xff800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;  // exclusive upper bound
-    float Tn = T_final;
-    float U0 = P.bg[0], U1 = P.bg[1], U2 = P.bg[2], UA = 0.f;
+    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
     int remaining = n_hits;
     int passes = 0;
     int st_node[kStackSize];
@@ -430,36 +605,11 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
         auto replay_front = [&]() {
             const int64_t key = keys[0];
             const int j = key_j(key);
-            const float4 g0 = __ldg(rec + 4 * j + 0);
-            const float4 g1 = __ldg(rec + 4 * j + 1);
-            const float4 g2 = __ldg(rec + 4 * j + 2);
-            const float4 sh = __ldg(rec + 4 * j + 3);
-            Hit h;
-            ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-            const float e = expf(__fmul_rn(-0.5f, h.D2));
-            const float a = __fmul_rn(sh.x, e);
-            const float om = __fsub_rn(1.f, a);
-            const float Ti = __fdiv_rn(Tn, om);
-            const float w = Ti * a;
-            // dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A))
-            const float dLda =
-                Ti * (gC[0] * (sh.y - U0) + gC[1] * (sh.z - U1) + gC[2] * (sh.w - U2) + gA * (1.f - UA));
-            U0 = fmaf(a, sh.y, om * U0);
-            U1 = fmaf(a, sh.z, om * U1);
-            U2 = fmaf(a, sh.w, om * U2);
-            UA = fmaf(om, UA, a);
-            Tn = Ti;
-            const float gD2 = -0.5f * a * dLda;
-            const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-            // dL/dm = -M^T (2 gD2 p)
-            const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);
-            const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
-            const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
+            float4 v[4];
+            adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, v);
             float4* gp = gtmp + 4 * j;
-            atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0));
-            atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1));
-            atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2));
-            atomicAdd(gp + 3, make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) atomicAdd(gp + k, v[k]);
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
@@ -503,7 +653,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                         ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                         if (COUNT) cnt.tests++;
                         if (h.hit) {
-                            const int64_t key = pack_key(h.t1, q);
+                            const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
                             if (key < hi_key && key > floor_key) {
                                 if (key > keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];  // evicted
@@ -636,59 +786,16 @@ __device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int
     }
 }
 
-// Running state of one ray's back-to-front replay: the transmittance in front of the next hit
-// to replay and the colour / alpha composited behind it (App. A.4-A.5).
-struct Adjoint {
-    float Tn, U0, U1, U2, UA;
-};
-
-// The adjoint of one composited hit (sorted Gaussian j), given the hits behind it: recovers
-// T_i = T_{i+1} / (1 - alpha_i), forms dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) + g_A (1 - U_A)),
-// advances U, and returns the 16-float contribution (dM rows + dm, dopacity + drgb) in v.
-// alpha comes from the same solve as in the forward pass, so it has the same bits.
-__device__ __forceinline__ void adjoint_hit(const float4* __restrict__ rec, int j, const float3 o, const float3 d,
-                                            const TraceParams& P, Adjoint& s, const float gC[3], float gA,
-                                            float4 (&v)[4]) {
-    const float4 g0 = __ldg(rec + 4 * j + 0);
-    const float4 g1 = __ldg(rec + 4 * j + 1);
-    const float4 g2 = __ldg(rec + 4 * j + 2);
-    const float4 sh = __ldg(rec + 4 * j + 3);
-    Hit h;
-    ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
-    const float e = expf(__fmul_rn(-0.5f, h.D2));
-    const float a = __fmul_rn(sh.x, e);
-    const float om = __fsub_rn(1.f, a);
-    const float Ti = __fdiv_rn(s.Tn, om);
-    const float w = Ti * a;
-    const float dLda =
-        Ti * (gC[0] * (sh.y - s.U0) + gC[1] * (sh.z - s.U1) + gC[2] * (sh.w - s.U2) + gA * (1.f - s.UA));
-    s.U0 = fmaf(a, sh.y, om * s.U0);
-    s.U1 = fmaf(a, sh.z, om * s.U1);
-    s.U2 = fmaf(a, sh.w, om * s.U2);
-    s.UA = fmaf(om, s.UA, a);
-    s.Tn = Ti;
-    const float gD2 = -0.5f * a * dLda;
-    const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-    const float dm0 = -(g0.x * q0 + g1.x * q1 + g2.x * q2);  // dL/dm = -M^T (2 gD2 p)
-    const float dm1 = -(g0.y * q0 + g1.y * q1 + g2.y * q2);
-    const float dm2 = -(g0.z * q0 + g1.z * q1 + g2.z * q2);
-    v[0] = make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], dm0);
-    v[1] = make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], dm1);
-    v[2] = make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], dm2);
-    v[3] = make_float4(dLda * e, gC[0] * w, gC[1] * w, gC[2] * w);
-}
-
 // ---------------------------------------------------------------------------------------------
 // List replay (the paper's index-buffer adjoint, Sec. 3 and Sec. 5): the forward pass wrote
 // the sorted ids of each ray's first list_cap composited hits; a ray with n <= list_cap hits is
 // replayed from that list back to front, with no traversal.  The whole warp calls it
 // (converged); lanes with n = 0 only take part in the scatter.
 // ---------------------------------------------------------------------------------------------
-template <bool COUNT>
+template <bool COUNT, bool DEPTH>
 __device__ __forceinline__ void replay_list(const float4* __restrict__ rec, const TraceParams& P, int64_t pix,
-                                            const float3 o, const float3 d, float T_final, int n, const float gC[3],
-                                            float gA, float4* __restrict__ gtmp, Counters& cnt, int* err) {
-    Adjoint s{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
+                                            const float3 o, const float3 d, float T_final, int n, const Upstream& g, float4* __restrict__ gtmp, Counters& cnt, int* err) {
+    Adjoint s{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
     const int* row = P.ids + (n > 0 ? pix * P.list_cap : 0);
     int k = n > 0 ? n : 0;
     while (__any_sync(0xffffffffu, k > 0)) {
@@ -698,7 +805,7 @@ __device__ __forceinline__ void replay_list(const float4* __restrict__ rec, cons
             --k;
             const int j = __ldg(row + k);
             if (j >= 0 && j < P.n_gauss) {
-                adjoint_hit(rec, j, o, d, P, s, gC, gA, v);
+                adjoint_hit<DEPTH>(rec, j, o, d, P, s, g, v);
                 jout = j;
                 if (COUNT) cnt.hits++;
             } else {  // a corrupt list: report and stop this ray
@@ -816,7 +923,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                             ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                             if (COUNT) cnt.tests++;
                             if (h.hit) {
-                                const int64_t key = pack_key(h.t1, q);
+                                const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
                                 if (key > lo_key && key < cap) {
                                     if (key < keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
@@ -902,19 +1009,19 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
     }
 }
 
-template <int K, bool COUNT>
+template <int K, bool COUNT, bool DEPTH>
 __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__ rec,
                                                       const float4* __restrict__ sph, const NodeSrc& nodes,
                                                       const TraceParams& P,
                                                       const float3 o, const float3 d, float T_final,
-                                                      int64_t last_key, int n_hits, const float gC[3], float gA,
+                                                      int64_t last_key, int n_hits, const Upstream& g,
                                                       float4* __restrict__ gtmp, Counters& cnt, int* err) {
     const unsigned FULL = 0xffffffffu;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float NINF = __int_as_float(0xff800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
+    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     int st_node[kStackSize];
@@ -938,7 +1045,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
-            adjoint_hit(rec, j, o, d, P, adj, gC, gA, vout);
+            adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, vout);
             jout = j;
             --remaining;
             hi_key = key;
@@ -996,7 +1103,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                             ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                             if (COUNT) cnt.tests++;
                             if (h.hit) {
-                                const int64_t key = pack_key(h.t1, q);
+                                const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
                                 if (key < hi_key && key > floor_key) {
                                     if (key > keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
@@ -1251,6 +1358,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKey;
         }
+        int nk = 0;  // pending keys (slots [0, nk))
         int64_t cap = kEmptyKey;
         const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
         auto composite_front = [&]() {
@@ -1272,16 +1380,19 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             last_key = key;
             if (COUNT) cnt.hits++;
             if (T < eps || count >= P.k_max) done = true;
-            kbuf_pop_front<K>(keys, kEmptyKey);
+            kbuf_pop_warp<K>(keys, nk, kEmptyKey, __activemask());
         };
         auto drop_cap = [&](float e) {  // a node with packet entry e was dropped for this pass
             if (active) {
                 cap = min(cap, pack_key(fmaxf(e, 0.f), 0));
                 // pending hits at or beyond the new cap may be preceded by hits of the dropped
                 // subtree: give them back (the next pass finds them again)
+                nk = 0;
 #pragma unroll
-                for (int s = 0; s < K; ++s)
+                for (int s = 0; s < K; ++s) {
                     if (keys[s] >= cap) keys[s] = kEmptyKey;
+                    nk += keys[s] != kEmptyKey;
+                }
             }
         };
         WarpQueue q;
@@ -1341,9 +1452,18 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
-                        for (int qq = start; qq < start + num; ++qq) {
+                        // sphere pre-test of the whole leaf, then one full test per Gaussian that
+                        // some lane may hit (in order: the same inserts as a sequential scan)
+                        const uint32_t mask = leaf_sphere_mask(sph, start, num, want, o, d);
+                        uint32_t todo = __reduce_or_sync(FULL, mask);
+                        while (todo) {
+                            const int g = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            const int qq = start + g;
                             if (COUNT && lane == 0) cnt.wleaf++;
-                            if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
+                            bool ins = false;
+                            int64_t ikey = 0;
+                            if ((mask >> g) & 1u) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
@@ -1351,11 +1471,12 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                 ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
                                 if (COUNT) cnt.tests++;
                                 if (hh.hit) {
-                                    const int64_t key = pack_key(hh.t1, qq);
+                                    const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
                                     if (key > lo_key && key < cap) {
                                         if (key < keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
-                                            kbuf_insert_asc<K>(keys, key);
+                                            ins = true;
+                                            ikey = key;
                                             if (COUNT) cnt.inserted++;
                                         } else {
                                             cap = key;
@@ -1363,6 +1484,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                     }
                                 }
                             }
+                            if (__any_sync(FULL, ins)) kbuf_insert_warp<K>(keys, nk, ins, ikey);
                         }
                     }
                 }
@@ -1403,11 +1525,10 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     }
 }
 
-template <int K, bool COUNT, int W>
+template <int K, bool COUNT, int W, bool DEPTH>
 __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                   const TraceParams& P, const float3 o, const float3 d,
-                                                  float T_final, int64_t last_key, int n_hits, const float gC[3],
-                                                  float gA, float4* __restrict__ gtmp, Counters& cnt, int* err) {
+                                                  float T_final, int64_t last_key, int n_hits, const Upstream& g, float4* __restrict__ gtmp, Counters& cnt, int* err) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -1415,7 +1536,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
     const float INF = __int_as_float(0x7f800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f};
+    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     while (__any_sync(FULL, remaining > 0)) {
@@ -1430,18 +1551,20 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         for (int s = 0; s < K; ++s) {
             keys[s] = kEmptyKeyDesc;
         }
+        int nk = 0;  // pending keys (slots [0, nk))
         int64_t floor_key = -1;
         const float thi = key_t(hi_key);
         bool stop = false;
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
             const int j = key_j(key);
-            adjoint_hit(rec, j, o, d, P, adj, gC, gA, vout);
+            adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, vout);
             jout = j;
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
             kbuf_pop_front<K>(keys, kEmptyKeyDesc);
+            --nk;
         };
         // warp-uniform replay: every lane takes part in the aggregated scatter
         auto replay_while = [&](auto cond) {
@@ -1457,9 +1580,12 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         auto drop_floor = [&](float x) {  // a node with packet exit x was dropped for this pass
             if (active) {
                 floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
+                nk = 0;
 #pragma unroll
-                for (int s = 0; s < K; ++s)
+                for (int s = 0; s < K; ++s) {
                     if (keys[s] <= floor_key) keys[s] = kEmptyKeyDesc;
+                    nk += keys[s] != kEmptyKeyDesc;
+                }
             }
         };
         WarpQueue q;
@@ -1516,9 +1642,16 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
-                        for (int qq = start; qq < start + num; ++qq) {
+                        const uint32_t mask = leaf_sphere_mask(sph, start, num, want, o, d);
+                        uint32_t todo = __reduce_or_sync(FULL, mask);
+                        while (todo) {
+                            const int g = __ffs(todo) - 1;
+                            todo &= todo - 1;
+                            const int qq = start + g;
                             if (COUNT && lane == 0) cnt.wleaf++;
-                            if (want && sphere_may_hit(o, d, __ldg(sph + qq))) {
+                            bool ins = false;
+                            int64_t ikey = 0;
+                            if ((mask >> g) & 1u) {
                                 const float4 g0 = __ldg(rec + 4 * qq + 0);
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
@@ -1526,11 +1659,12 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                 ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
                                 if (COUNT) cnt.tests++;
                                 if (hh.hit) {
-                                    const int64_t key = pack_key(hh.t1, qq);
+                                    const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
                                     if (key < hi_key && key > floor_key) {
                                         if (key > keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
-                                            kbuf_insert_desc<K>(keys, key);
+                                            ins = true;
+                                            ikey = key;
                                             if (COUNT) cnt.inserted++;
                                         } else {
                                             floor_key = key;
@@ -1538,6 +1672,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                     }
                                 }
                             }
+                            if (__any_sync(FULL, ins)) kbuf_insert_warp<K, true>(keys, nk, ins, ikey);
                         }
                     }
                 }
@@ -1597,419 +1732,6 @@ __device__ __forceinline__ bool tile_pixel(const FwdArgs& A, int64_t tile, int l
     py = ty * (32 / A.tile_w) + (lane / A.tile_w);
     pix = cam.pix_base + (int64_t)py * cam.W + px;
     return px < cam.W && py < cam.H && ty < cam.tiles_y;
-}
-
-template <int K, bool PERSIST, bool COUNT, int MODE>
-__global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
-    extern __shared__ float4 s_top[];
-    if (MODE != 3)
-        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
-    __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
-                     A.P.n_gauss, A.err};
-    const int lane = threadIdx.x & 31;
-    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    Counters cnt;
-    uint32_t rays = 0;
-    while (true) {
-        if (PERSIST) {
-            unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(A.queue, 1ull);
-            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
-        }
-        if (tile >= A.total_tiles) break;
-        DevCam cam;
-        int px, py;
-        int64_t pix;
-        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
-        float C0, C1, C2, T, depth;
-        int64_t last_key;
-        int count;
-        float3 o, d;
-        camera_ray(cam, px, py, o, d);
-        if (MODE == 3)
-            trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
-                                          cnt, A.err);
-        else if (MODE == 2)
-            trace_forward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
-                                          cnt, A.err);
-        else if (MODE == 1)
-            trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
-                                           cnt, A.err);
-        else if (valid)
-            trace_forward<K, COUNT>(A.rec, A.sph, ns, A.P, pix, o, d, C0, C1, C2, T, depth, last_key, count, cnt, A.err);
-        if (valid) {
-            A.rgb[3 * pix + 0] = fmaf(T, A.P.bg[0], C0);
-            A.rgb[3 * pix + 1] = fmaf(T, A.P.bg[1], C1);
-            A.rgb[3 * pix + 2] = fmaf(T, A.P.bg[2], C2);
-            A.alpha[pix] = 1.f - T;
-            if (A.depth) A.depth[pix] = depth;
-            A.sT[pix] = T;
-            A.skey[pix] = last_key;
-            A.sn[pix] = count;
-            if (COUNT) ++rays;
-        }
-        if (!PERSIST) break;
-    }
-    if (COUNT) {
-        unsigned long long v[kNumStats] = {rays, cnt.nodes, cnt.tests, cnt.hits, cnt.rounds,
-                                           cnt.inserted, 0, 0, cnt.wnodes, cnt.wleaf};
-#pragma unroll
-        for (int k = 0; k < kNumStats; ++k) {
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kNumStats; ++k)
-                if (v[k]) atomicAdd(A.stats + k, v[k]);
-        }
-    }
-}
-
-// List replay (adjoint, first launch): one warp per ray tile of the forward pass; every ray
-// whose hits all fit in its hit list is replayed from it (replay_list).  A tile holding a ray
-// with more hits is appended to the overflow list, which k_render_bwd re-traverses next.
-template <bool PERSIST, bool COUNT>
-__global__ void __launch_bounds__(128) k_replay_list(FwdArgs A, BwdArgs B) {
-    const int lane = threadIdx.x & 31;
-    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    Counters cnt;
-    uint32_t rays = 0;
-    uint64_t listed = 0;
-    while (true) {
-        if (PERSIST) {
-            unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(A.queue + 1, 1ull);
-            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
-        }
-        if (tile >= A.total_tiles) break;
-        DevCam cam;
-        int px, py;
-        int64_t pix;
-        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
-        const int n = valid ? A.sn[pix] : 0;
-        const int nl = n <= A.P.list_cap ? n : 0;
-        float3 o, d;
-        camera_ray(cam, px, py, o, d);
-        float gC[3] = {0.f, 0.f, 0.f};
-        float gA = 0.f, Tf = 1.f;
-        if (nl > 0) {
-            gC[0] = B.d_rgb[3 * pix];
-            gC[1] = B.d_rgb[3 * pix + 1];
-            gC[2] = B.d_rgb[3 * pix + 2];
-            gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
-            Tf = A.sT[pix];
-        }
-        if (COUNT && n > 0) ++rays;
-        if (COUNT) listed += nl;
-        replay_list<COUNT>(A.rec, A.P, pix, o, d, Tf, nl, gC, gA, B.gtmp, cnt, A.err);
-        if (__any_sync(0xffffffffu, n > A.P.list_cap) && lane == 0) {
-            const int64_t global = A.cam_single < 0 ? tile : A.cams[A.cam_single].tile_base + tile;
-            const unsigned long long slot = atomicAdd(A.queue + 3, 1ull);
-            if (slot < (unsigned long long)B.ovf_cap) B.ovf[slot] = (int)global;
-            else atomicOr(A.err, kErrIndex);
-        }
-        if (!PERSIST) break;
-    }
-    if (COUNT) {
-        unsigned long long v[kNumStats] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed, 0, 0};
-#pragma unroll
-        for (int k = 0; k < kNumStats; ++k) {
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kNumStats; ++k)
-                if (v[k]) atomicAdd(A.stats + k, v[k]);
-        }
-    }
-}
-
-template <int K, bool PERSIST, bool COUNT, int MODE>
-__global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
-    extern __shared__ float4 s_top[];
-    if (B.ovf && A.queue[3] == 0) return;  // every ray was replayed from its hit list
-    if (MODE != 3)
-        for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
-    __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
-                     A.P.n_gauss, A.err};
-    const int lane = threadIdx.x & 31;
-    // with a hit list, only the tiles the list replay found overflowing are re-traversed
-    const int64_t n_tiles = B.ovf ? (int64_t)min((unsigned long long)B.ovf_cap, A.queue[3]) : A.total_tiles;
-    int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    Counters cnt;
-    uint32_t rays = 0, retraced = 0;
-    while (true) {
-        if (PERSIST) {
-            unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(A.queue + 2, 1ull);
-            tile = (int64_t)__shfl_sync(0xffffffffu, t, 0);
-        }
-        if (tile >= n_tiles) break;
-        if (B.ovf) tile = B.ovf[tile];
-        DevCam cam;
-        int px, py;
-        int64_t pix;
-        const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
-        const int n = valid ? A.sn[pix] : 0;
-        const int nt = n > A.P.list_cap ? n : 0;  // rays the hit list cannot replay
-        float3 o, d;
-        camera_ray(cam, px, py, o, d);
-        float gC[3] = {0.f, 0.f, 0.f};
-        float gA = 0.f, Tf = 1.f;
-        int64_t lk = -1;
-        if (nt > 0) {
-            gC[0] = B.d_rgb[3 * pix];
-            gC[1] = B.d_rgb[3 * pix + 1];
-            gC[2] = B.d_rgb[3 * pix + 2];
-            gA = B.d_alpha ? B.d_alpha[pix] : 0.f;
-            Tf = A.sT[pix];
-            lk = A.skey[pix];
-            if (COUNT) {
-                ++retraced;
-                if (A.P.list_cap == 0) ++rays;
-            }
-        }
-        if (MODE == 3)
-            trace_backward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
-        else if (MODE == 2)
-            trace_backward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
-        else if (MODE == 1)
-            trace_backward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
-        else if (nt > 0)
-            trace_backward<K, COUNT>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, gC, gA, B.gtmp, cnt, A.err);
-        if (!PERSIST) break;
-    }
-    if (COUNT) {
-        unsigned long long v[kNumStats] = {rays,     cnt.nodes, cnt.tests, cnt.hits,   cnt.rounds,
-                                           cnt.inserted, retraced, 0,        cnt.wnodes, cnt.wleaf};
-#pragma unroll
-        for (int k = 0; k < kNumStats; ++k) {
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], s);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < kNumStats; ++k) atomicAdd(A.stats + k, v[k]);
-        }
-    }
-}
-
-// dL/dM, dL/dm, dL/dopacity, dL/drgb (Morton order) -> caller's gradients (Gaussian ids).
-// M = S^-1 R^T:  dL/ds_k = -(1/s_k) sum_l G[k][l] M[k][l];  dL/dR[l][k] = G[k][l] / s_k;
-// R = I + s_q K(q), s_q = 2/|q|^2 (App. A.6):  dR/dq_x = -s_q^2 q_x K + s_q dK/dq_x.
-__global__ void k_finalize(const float4* __restrict__ gtmp, const float4* __restrict__ rec,
-                           const uint32_t* __restrict__ perm, const float* __restrict__ quats,
-                           const float* __restrict__ scales, int64_t n, rs_gaussian_grads out) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int64_t i = perm[j];
-    const float4 G0 = gtmp[4 * j], G1 = gtmp[4 * j + 1], G2 = gtmp[4 * j + 2], G3 = gtmp[4 * j + 3];
-    if (out.d_means) {
-        out.d_means[3 * i] += G0.w;
-        out.d_means[3 * i + 1] += G1.w;
-        out.d_means[3 * i + 2] += G2.w;
-    }
-    if (out.d_opacities) out.d_opacities[i] += G3.x;
-    if (out.d_rgb) {
-        out.d_rgb[3 * i] += G3.y;
-        out.d_rgb[3 * i + 1] += G3.z;
-        out.d_rgb[3 * i + 2] += G3.w;
-    }
-    if (!out.d_scales && !out.d_quats) return;
-    const float GM[3][3] = {{G0.x, G0.y, G0.z}, {G1.x, G1.y, G1.z}, {G2.x, G2.y, G2.z}};
-    const float4 m0 = rec[4 * j], m1 = rec[4 * j + 1], m2 = rec[4 * j + 2];
-    const float M[3][3] = {{m0.x, m0.y, m0.z}, {m1.x, m1.y, m1.z}, {m2.x, m2.y, m2.z}};
-    const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
-    if (out.d_scales) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            out.d_scales[3 * i + k] += -(GM[k][0] * M[k][0] + GM[k][1] * M[k][1] + GM[k][2] * M[k][2]) / s[k];
-    }
-    if (out.d_quats) {
-        const float qa = quats[4 * i], qb = quats[4 * i + 1], qc = quats[4 * i + 2], qd = quats[4 * i + 3];
-        const float sq = 2.f / (qa * qa + qb * qb + qc * qc + qd * qd);
-        float GR[3][3];  // dL/dR[l][k]
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) GR[l][k] = GM[k][l] / s[k];
-        const float Kq[3][3] = {{-(qc * qc + qd * qd), qb * qc - qa * qd, qb * qd + qa * qc},
-                                {qb * qc + qa * qd, -(qb * qb + qd * qd), qc * qd - qa * qb},
-                                {qb * qd - qa * qc, qc * qd + qa * qb, -(qb * qb + qc * qc)}};
-        float GK = 0.f;
-#pragma unroll
-        for (int l = 0; l < 3; ++l)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) GK += GR[l][k] * Kq[l][k];
-        // sum over entries of GR (.) dK/dq_x
-        const float da = GR[0][1] * (-qd) + GR[0][2] * qc + GR[1][0] * qd + GR[1][2] * (-qb) + GR[2][0] * (-qc) +
-                         GR[2][1] * qb;
-        const float db = GR[0][1] * qc + GR[0][2] * qd + GR[1][0] * qc + GR[1][1] * (-2.f * qb) + GR[1][2] * (-qa) +
-                         GR[2][0] * qd + GR[2][1] * qa + GR[2][2] * (-2.f * qb);
-        const float dc = GR[0][0] * (-2.f * qc) + GR[0][1] * qb + GR[0][2] * qa + GR[1][0] * qb + GR[1][2] * qd +
-                         GR[2][0] * (-qa) + GR[2][1] * qd + GR[2][2] * (-2.f * qc);
-        const float dd = GR[0][0] * (-2.f * qd) + GR[0][1] * (-qa) + GR[0][2] * qb + GR[1][0] * qa +
-                         GR[1][1] * (-2.f * qd) + GR[1][2] * qc + GR[2][0] * qb + GR[2][1] * qc;
-        const float ns = -sq * sq * GK;
-        out.d_quats[4 * i] += ns * qa + sq * da;
-        out.d_quats[4 * i + 1] += ns * qb + sq * db;
-        out.d_quats[4 * i + 2] += ns * qc + sq * dc;
-        out.d_quats[4 * i + 3] += ns * qd + sq * dd;
-    }
-}
-
-__global__ void k_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px, const int32_t* py,
-                             float* o, float* d) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    float3 oo, dd;
-    camera_ray(cams[ci[r]], px[r], py[r], oo, dd);
-    o[3 * r] = oo.x; o[3 * r + 1] = oo.y; o[3 * r + 2] = oo.z;
-    d[3 * r] = dd.x; d[3 * r + 1] = dd.y; d[3 * r + 2] = dd.z;
-}
-
-__global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs, const float* ro, const float* rd,
-                             const int32_t* sj, float Q, float t_near, float* out) {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= n_pairs) return;
-    const int j = sj[k];
-    if (j < 0 || j >= n_gauss) {  // out-of-range id: report NaN instead of reading
-        out[4 * k] = out[4 * k + 1] = out[4 * k + 2] = out[4 * k + 3] = __int_as_float(0x7fc00000);
-        return;
-    }
-    Hit h;
-    ray_ellipsoid<false>(make_float3(ro[3 * k], ro[3 * k + 1], ro[3 * k + 2]),
-                         make_float3(rd[3 * k], rd[3 * k + 1], rd[3 * k + 2]), rec[4 * j], rec[4 * j + 1],
-                         rec[4 * j + 2], Q, t_near, h);
-    out[4 * k] = h.D2;
-    out[4 * k + 1] = h.t1;
-    out[4 * k + 2] = h.hit ? 1.f : 0.f;
-    out[4 * k + 3] = response_alpha(rec[4 * j + 3].x, h.D2);
-}
-
-// ---------------------------------------------------------------------------------------------
-// host launchers
-// ---------------------------------------------------------------------------------------------
-template <int K, bool PERSIST, bool COUNT, int MODE>
-static int occupancy_of(bool backward, int block, size_t smem) {
-    int nb = 0;
-    if (backward)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_bwd<K, PERSIST, COUNT, MODE>, block, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, PERSIST, COUNT, MODE>, block, smem);
-    return nb;
-}
-
-template <int K, bool COUNT>
-static int occupancy_m(bool backward, int block, int mode, size_t smem) {
-    if (mode == 3) return occupancy_of<K, true, COUNT, 3>(backward, block, 0);
-    if (mode == 2) return occupancy_of<K, true, COUNT, 2>(backward, block, smem);
-    if (mode == 1) return occupancy_of<K, true, COUNT, 1>(backward, block, smem);
-    return occupancy_of<K, true, COUNT, 0>(backward, block, smem);
-}
-
-static size_t smem_bytes(int n_top) { return (size_t)n_top * 4 * sizeof(float4); }
-
-int persistent_grid(bool backward, int K, int block, bool count, int mode, int n_top, int sms) {
-    const size_t sm = smem_bytes(n_top);
-    int nb = 1;
-    if (K == 8) nb = count ? occupancy_m<8, true>(backward, block, mode, sm) : occupancy_m<8, false>(backward, block, mode, sm);
-    else if (K == 16)
-        nb = count ? occupancy_m<16, true>(backward, block, mode, sm) : occupancy_m<16, false>(backward, block, mode, sm);
-    else nb = count ? occupancy_m<32, true>(backward, block, mode, sm) : occupancy_m<32, false>(backward, block, mode, sm);
-    return std::max(1, nb) * sms;
-}
-
-template <int K, bool PERSIST, bool COUNT, int MODE>
-static void launch_one(bool backward, const FwdArgs& A, const BwdArgs* B, int grid, int block, cudaStream_t st) {
-    const size_t sm = MODE == 3 ? 0 : smem_bytes(A.n_top);
-    if (backward) k_render_bwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A, *B);
-    else k_render_fwd<K, PERSIST, COUNT, MODE><<<grid, block, sm, st>>>(A);
-}
-
-template <int K, bool PERSIST, bool COUNT>
-static void launch_mode(bool backward, const FwdArgs& A, const BwdArgs* B, int mode, int grid, int block,
-                        cudaStream_t st) {
-    if (mode == 3) launch_one<K, PERSIST, COUNT, 3>(backward, A, B, grid, block, st);
-    else if (mode == 2) launch_one<K, PERSIST, COUNT, 2>(backward, A, B, grid, block, st);
-    else if (mode == 1) launch_one<K, PERSIST, COUNT, 1>(backward, A, B, grid, block, st);
-    else launch_one<K, PERSIST, COUNT, 0>(backward, A, B, grid, block, st);
-}
-
-template <int K>
-static void launch_kp(bool backward, const FwdArgs& A, const BwdArgs* B, bool persistent, bool count, int mode,
-                      int grid, int block, cudaStream_t st) {
-    if (persistent) {
-        if (count) launch_mode<K, true, true>(backward, A, B, mode, grid, block, st);
-        else launch_mode<K, true, false>(backward, A, B, mode, grid, block, st);
-    } else {
-        if (count) launch_mode<K, false, true>(backward, A, B, mode, grid, block, st);
-        else launch_mode<K, false, false>(backward, A, B, mode, grid, block, st);
-    }
-}
-
-cudaError_t launch_forward(const FwdArgs& A, int K, bool persistent, bool count, int mode, int grid, int block,
-                           cudaStream_t st) {
-    if (K == 8) launch_kp<8>(false, A, nullptr, persistent, count, mode, grid, block, st);
-    else if (K == 16) launch_kp<16>(false, A, nullptr, persistent, count, mode, grid, block, st);
-    else if (K == 32) launch_kp<32>(false, A, nullptr, persistent, count, mode, grid, block, st);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool persistent, bool count, int mode,
-                            int grid, int block, cudaStream_t st) {
-    if (K == 8) launch_kp<8>(true, A, &B, persistent, count, mode, grid, block, st);
-    else if (K == 16) launch_kp<16>(true, A, &B, persistent, count, mode, grid, block, st);
-    else if (K == 32) launch_kp<32>(true, A, &B, persistent, count, mode, grid, block, st);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-template <bool PERSIST, bool COUNT>
-static int list_occupancy(int block) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_replay_list<PERSIST, COUNT>, block, 0);
-    return nb;
-}
-
-int list_replay_grid(bool count, int block, int sms) {
-    const int nb = count ? list_occupancy<true, true>(block) : list_occupancy<true, false>(block);
-    return std::max(1, nb) * sms;
-}
-
-cudaError_t launch_list_replay(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
-                               cudaStream_t st) {
-    if (persistent) {
-        if (count) k_replay_list<true, true><<<grid, block, 0, st>>>(A, B);
-        else k_replay_list<true, false><<<grid, block, 0, st>>>(A, B);
-    } else {
-        if (count) k_replay_list<false, true><<<grid, block, 0, st>>>(A, B);
-        else k_replay_list<false, false><<<grid, block, 0, st>>>(A, B);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const float4* gtmp, const float4* rec, const uint32_t* perm, const float* quats,
-                            const float* scales, int64_t n, const rs_gaussian_grads& out, cudaStream_t st) {
-    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(gtmp, rec, perm, quats, scales, n, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_debug_rays(const DevCam* cams, int64_t n, const int32_t* ci, const int32_t* px, const int32_t* py,
-                              float* o, float* d, cudaStream_t st) {
-    k_debug_rays<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cams, n, ci, px, py, o, d);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_debug_hits(const float4* rec, int64_t n_gauss, int64_t n, const float* ro, const float* rd,
-                              const int32_t* sj, float Q, float t_near, float* out, cudaStream_t st) {
-    k_debug_hits<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(rec, n_gauss, n, ro, rd, sj, Q, t_near, out);
-    return cudaGetLastError();
 }
 
 }  // namespace rs

@@ -36,7 +36,7 @@ class RsFrame(ctypes.Structure):
 
 
 class RsFrameGrad(ctypes.Structure):
-    _fields_ = [("d_rgb", P), ("d_alpha", P)]
+    _fields_ = [("d_rgb", P), ("d_alpha", P), ("d_depth", P)]
 
 
 class RsGaussianGrads(ctypes.Structure):
@@ -74,6 +74,11 @@ _SIGS = {
     "rs_debug_rays": (i32, [P, i32, i64, P, P, P, P, P, P]),
     "rs_debug_hits": (i32, [P, i64, P, P, P, f32, f32, P, P]),
     "rs_test_fail_alloc": (i32, [i64]),
+    "rs_loss_l2_dssim": (i32, [P, P, P, i32, f32, P, P, P, P]),
+    "rs_loss_state_destroy": (i32, [P]),
+    "rs_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
+    "rs_sigmoid": (i32, [P, P, i64, P]),
+    "rs_sigmoid_backward": (i32, [P, P, P, i64, P]),
 }
 
 _LIB = None

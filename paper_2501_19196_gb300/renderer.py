@@ -29,12 +29,13 @@ class RenderParams:
     t_near: float = 0.0
     background: tuple = (0.0, 0.0, 0.0)
     k_max: int = 2 ** 31 - 1
+    sort_key: int = 0  # 0: order hits by entry t1; 1: by t_m (maximum response)
 
     def to_c(self) -> native.RsRenderParams:
         p = native.RsRenderParams()
         p.Q, p.eps1, p.t_near = float(self.Q), float(self.eps1), float(self.t_near)
         p.background[:] = [float(x) for x in self.background]
-        p.k_max, p.depth_mode, p.sort_key = int(self.k_max), 0, 0
+        p.k_max, p.depth_mode, p.sort_key = int(self.k_max), 0, int(self.sort_key)
         return p
 
 
@@ -115,8 +116,9 @@ class Renderer:
         return out
 
     # -- backward ----------------------------------------------------------------------------
-    def backward(self, d_rgb, d_alpha=None, grads=None, stream=None, stats=None):
-        """Accumulate dL/d(params) into `grads` (dict of zeroed tensors, created if None)."""
+    def backward(self, d_rgb, d_alpha=None, grads=None, stream=None, stats=None, d_depth=None):
+        """Accumulate dL/d(params) into `grads` (dict of zeroed tensors, created if None) for the
+        upstream gradients of rgb (required), alpha and depth (optional)."""
         means = self._keep[0]
         n = means.shape[0]
         if grads is None:
@@ -127,7 +129,10 @@ class Renderer:
             raise ValueError("d_rgb: expected a contiguous (P, 3) tensor")
         if d_alpha is not None and (not d_alpha.is_contiguous() or d_alpha.numel() != self.n_pixels):
             raise ValueError("d_alpha: expected a contiguous (P,) tensor")
-        dl = native.RsFrameGrad(d_rgb.data_ptr(), None if d_alpha is None else d_alpha.data_ptr())
+        if d_depth is not None and (not d_depth.is_contiguous() or d_depth.numel() != self.n_pixels):
+            raise ValueError("d_depth: expected a contiguous (P,) tensor")
+        dl = native.RsFrameGrad(d_rgb.data_ptr(), None if d_alpha is None else d_alpha.data_ptr(),
+                                None if d_depth is None else d_depth.data_ptr())
         out = native.RsGaussianGrads(*[None if grads.get(k) is None else grads[k].data_ptr()
                                        for k in ("means", "quats", "scales", "opacities", "rgb")])
         if stats is None:
@@ -200,7 +205,6 @@ class _RenderFn(torch.autograd.Function):
         renderer.build(means, quats, scales, opacities, rgb)
         out_rgb, out_alpha, out_depth = renderer.render(cams, params)
         ctx.renderer = renderer
-        ctx.mark_non_differentiable(out_depth)
         return out_rgb, out_alpha, out_depth
 
     @staticmethod
@@ -208,14 +212,15 @@ class _RenderFn(torch.autograd.Function):
         r = ctx.renderer
         g_rgb = torch.zeros((r.n_pixels, 3), device=r._keep[0].device) if g_rgb is None else g_rgb.contiguous()
         g_alpha = None if g_alpha is None else g_alpha.contiguous()
-        grads = r.backward(g_rgb, g_alpha)
+        g_depth = None if g_depth is None else g_depth.contiguous()
+        grads = r.backward(g_rgb, g_alpha, d_depth=g_depth)
         return grads["means"], grads["quats"], grads["scales"], grads["opacities"], grads["rgb"], None, None, None
 
 
 def render_gaussians(means, quats, scales, opacities, rgb, cams, params: RenderParams | None = None,
                      renderer: Renderer | None = None):
     """Differentiable render of every camera in `cams`; returns (rgb, alpha, depth) per pixel.
-    The depth output carries no gradient."""
+    All three outputs carry gradients (depth through opacities and the hits' sort keys)."""
     renderer = renderer or Renderer()
     return _RenderFn.apply(means.contiguous(), quats.contiguous(), scales.contiguous(), opacities.contiguous(),
                            rgb.contiguous(), renderer, cams, params or RenderParams())

@@ -15,10 +15,10 @@ def to_dev(scene, device="cuda"):
     return f(scene.means), f(scene.quats), f(scene.scales), f(scene.opacities), f(scene.rgb)
 
 
-def params(Q=None, eps1=1e-4, k_max=2 ** 31 - 1, background=(0.0, 0.0, 0.0), t_near=0.0):
+def params(Q=None, eps1=1e-4, k_max=2 ** 31 - 1, background=(0.0, 0.0, 0.0), t_near=0.0, sort_key=0):
     from paper_2501_19196_gb300 import RenderParams
     return RenderParams(Q=scenes.default_Q() if Q is None else Q, eps1=eps1, t_near=t_near,
-                        background=tuple(background), k_max=k_max)
+                        background=tuple(background), k_max=k_max, sort_key=sort_key)
 
 
 def gpu_render(scene, cams, prm, tune=None, renderer=None, keep=False):
@@ -42,9 +42,9 @@ def pixel_index(cams, cam, px, py):
     return base[cam] + py.astype(np.int64) * cams.width[cam].astype(np.int64) + px
 
 
-def oracle_pixels(scene, cams, cam, px, py, prm, dl_rgb=None, dl_alpha=None):
+def oracle_pixels(scene, cams, cam, px, py, prm, dl_rgb=None, dl_alpha=None, dl_depth=None):
     return oracle.render(scene, cams, cam, px, py, prm.Q, prm.eps1, prm.k_max, prm.background, prm.t_near,
-                         dl_rgb=dl_rgb, dl_alpha=dl_alpha)
+                         dl_rgb=dl_rgb, dl_alpha=dl_alpha, sort_key=prm.sort_key, dl_depth=dl_depth)
 
 
 def compare_image(gpu, ora, idx, tol=TOL_RGB, max_masked=0.02, label=""):

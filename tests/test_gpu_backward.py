@@ -21,7 +21,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _grad_case(sc, cams, prm, tune=None, stride=1, seed=1, with_alpha=True):
+def _grad_case(sc, cams, prm, tune=None, stride=1, seed=1, with_alpha=True, with_depth=False):
     from paper_2501_19196_gb300 import native
     cam, px, py = scenes.pixel_grid(cams, stride=stride)
     idx = pixel_index(cams, cam, px, py)
@@ -29,18 +29,24 @@ def _grad_case(sc, cams, prm, tune=None, stride=1, seed=1, with_alpha=True):
     rng = np.random.default_rng(seed)
     gc_s = rng.standard_normal((len(cam), 3))
     ga_s = rng.standard_normal(len(cam)) if with_alpha else np.zeros(len(cam))
+    gd_s = rng.standard_normal(len(cam)) if with_depth else np.zeros(len(cam))
     ora0 = oracle_pixels(sc, cams, cam, px, py, prm)
     bad = (ora0["mask"] & oracle.AMB_DECISION) != 0
     gc_s[bad] = 0.0
     ga_s[bad] = 0.0
-    ora = oracle_pixels(sc, cams, cam, px, py, prm, dl_rgb=gc_s, dl_alpha=ga_s)
+    gd_s[bad] = 0.0
+    ora = oracle_pixels(sc, cams, cam, px, py, prm, dl_rgb=gc_s, dl_alpha=ga_s,
+                        dl_depth=gd_s if with_depth else None)
     # full-frame upstream gradient: zero except at the listed pixels
     gc = np.zeros((P, 3), np.float32)
     ga = np.zeros(P, np.float32)
+    gd = np.zeros(P, np.float32)
     gc[idx] = gc_s
     ga[idx] = ga_s
+    gd[idx] = gd_s
     out, r, dev = gpu_render(sc, cams, prm, tune=tune or native.default_tune(), keep=True)
-    grads = r.backward(torch.from_numpy(gc).cuda(), torch.from_numpy(ga).cuda())
+    grads = r.backward(torch.from_numpy(gc).cuda(), torch.from_numpy(ga).cuda(),
+                       d_depth=torch.from_numpy(gd).cuda() if with_depth else None)
     torch.cuda.synchronize()
     r.check_device()
     r.close()
@@ -57,6 +63,22 @@ def test_gradients_tiny_scenes(seed):
     for kw in (dict(), dict(eps1=0.2), dict(k_max=2), dict(background=(0.3, 0.2, 1.0))):
         errs, bad = _grad_case(sc, cams, params(**kw), seed=seed)
         assert max(errs.values()) < TOL_GRAD, (kw, errs)
+
+
+@pytest.mark.parametrize("sort_key", [0, 1])
+@pytest.mark.parametrize("seed", range(4))
+def test_depth_gradients_tiny_scenes(seed, sort_key):
+    """Exact gradient of sum_i w_i t_i (with rgb and alpha terms) for both sort keys, through
+    the hit-list replay and through every re-traversing adjoint."""
+    from paper_2501_19196_gb300 import native
+    sc = scenes.random_tiny_scene(320 + seed, n=40, flat_frac=0.3 if seed % 2 else 0.0)
+    cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 21, 17, 55.0),
+                                  scenes.look_at_camera((-3.0, 0.5, 0.7), (0.1, 0, 0), 16, 16, 45.0)])
+    for kw, tune in ((dict(), dict()), (dict(eps1=0.2), dict(hit_list=0)), (dict(k_max=3), dict(hit_list=0, traversal=0)),
+                     (dict(background=(0.3, 0.2, 1.0)), dict(hit_list=0, traversal=1))):
+        errs, bad = _grad_case(sc, cams, params(sort_key=sort_key, **kw), tune=native.default_tune(**tune), seed=seed,
+                               with_depth=True)
+        assert max(errs.values()) < TOL_GRAD, (kw, tune, errs)
 
 
 def test_gradients_workload_1k_full_frame():
@@ -138,12 +160,13 @@ def test_autograd_function_matches_direct_backward():
     rng = np.random.default_rng(0)
     w = torch.from_numpy(rng.standard_normal((rgb.shape[0], 3)).astype(np.float32)).cuda()
     wa = torch.from_numpy(rng.standard_normal(rgb.shape[0]).astype(np.float32)).cuda()
-    loss = (rgb * w).sum() + (alpha * wa).sum()
+    wd = torch.from_numpy(rng.standard_normal(rgb.shape[0]).astype(np.float32)).cuda()
+    loss = (rgb * w).sum() + (alpha * wa).sum() + (depth * wd).sum()
     loss.backward()
     r = Renderer()
     r.build(*to_dev(sc))
     r.render(cams, prm)
-    ref = r.backward(w.contiguous(), wa.contiguous())
+    ref = r.backward(w.contiguous(), wa.contiguous(), d_depth=wd.contiguous())
     torch.cuda.synchronize()
     # float atomics accumulate in a different order on each call: compare in relative L2
     for leaf, k in zip(leaves, KEYS):

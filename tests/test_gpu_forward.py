@@ -168,6 +168,7 @@ def test_forward_workload_1k_full_frame():
 CASES = [
     dict(eps1=1e-4), dict(eps1=0.0), dict(eps1=0.3), dict(k_max=1), dict(k_max=3), dict(k_max=16),
     dict(Q=4.0), dict(Q=9.0), dict(Q=16.0), dict(background=(0.2, 0.5, 1.0)), dict(t_near=2.9),
+    dict(sort_key=1), dict(sort_key=1, eps1=0.3, k_max=5), dict(sort_key=1, t_near=2.9),
 ]
 
 
@@ -224,6 +225,13 @@ def test_tunables_and_launch_modes_bit_identical():
                                   scenes.look_at_camera((-2.0, -2.5, 1.5), (0, 0, 0), 33, 70, 60)])
     prm = params(eps1=1e-3, background=(1, 1, 1))
     ref = gpu_render(sc, cams, prm, tune=native.default_tune())
+    prm1 = params(eps1=1e-3, background=(1, 1, 1), sort_key=1)
+    ref1 = gpu_render(sc, cams, prm1, tune=native.default_tune())
+    for kw in (dict(traversal=0), dict(traversal=1), dict(traversal=3), dict(kbuf=8, leaf_size=1),
+               dict(persistent=0, tile_w=4)):
+        out = gpu_render(sc, cams, prm1, tune=native.default_tune(**kw))
+        for k in ("rgb", "alpha", "depth"):
+            np.testing.assert_array_equal(out[k], ref1[k], err_msg="sort_key 1 " + str(kw))
     for kw in (dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(leaf_size=8), dict(leaf_size=16),
                dict(tile_w=4), dict(tile_w=16), dict(tile_w=32), dict(persistent=0), dict(morton_bits=10),
                dict(morton_bits=20), dict(traversal=0), dict(traversal=0, leaf_size=1, kbuf=8),
