@@ -22,14 +22,15 @@ from .build import build_oracle, library_path
 
 _LIB = None
 
-AMB_BOUNDARY, AMB_TIE, AMB_EPS1, AMB_TNEAR, AMB_IMPACT = 1, 2, 4, 8, 16
-AMB_DECISION = AMB_BOUNDARY | AMB_TIE | AMB_EPS1 | AMB_TNEAR
+AMB_BOUNDARY, AMB_TIE, AMB_EPS1, AMB_TNEAR, AMB_IMPACT, AMB_EPS2 = 1, 2, 4, 8, 16, 256
+AMB_DECISION = AMB_BOUNDARY | AMB_TIE | AMB_EPS1 | AMB_TNEAR | AMB_EPS2
 IMP_BOUNDARY, IMP_TIE, IMP_EPS1 = 32, 64, 128
 
 
 class OrParams(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_double), ("eps1", ctypes.c_double), ("t_near", ctypes.c_double),
-                ("bg", ctypes.c_double * 3), ("k_max", ctypes.c_int32), ("sort_key", ctypes.c_int32)]
+                ("bg", ctypes.c_double * 3), ("k_max", ctypes.c_int32), ("sort_key", ctypes.c_int32),
+                ("eps2", ctypes.c_double), ("grad_mode", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def lib():
@@ -114,12 +115,13 @@ def quat_to_rot(q):
 
 def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background=(0, 0, 0),
                 t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, params64=None, sort_key=0,
-                dl_depth=None):
+                dl_depth=None, eps2=None):
     """Render explicit rays.  `scene` fields are converted to float64 exactly (or taken from
     `params64`, a dict of float64 arrays, for finite differences).  sort_key 0 orders hits by
     the entry t1, 1 by the maximum-response parameter t_m.  Returns a dict with rgb (R,3),
     alpha, depth, T, n_hits, mask and, when dl_rgb or dl_depth is given, the float64
-    gradients of <dl_rgb, rgb> + <dl_alpha, alpha> + <dl_depth, depth>."""
+    gradients of <dl_rgb, rgb> + <dl_alpha, alpha> + <dl_depth, depth> (with eps2 given: the
+    paper's eps2 estimator for the last composited hit of each ray cut by eps1)."""
     src = params64 if params64 is not None else {
         "means": scene.means, "quats": scene.quats, "scales": scene.scales,
         "opacities": scene.opacities, "rgb": scene.rgb}
@@ -129,7 +131,8 @@ def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background
     ray_o, ray_d = _c(ray_o, np.float64), _c(ray_d, np.float64)
     R = ray_o.shape[0]
     prm = OrParams(float(Q), float(eps1), float(t_near), (ctypes.c_double * 3)(*background),
-                   int(k_max), int(sort_key))
+                   int(k_max), int(sort_key), float(eps2 if eps2 is not None else 0.0),
+                   1 if eps2 is not None else 0, 0)
     out = {"rgb": np.zeros((R, 3)), "alpha": np.zeros(R), "depth": np.zeros(R),
            "T": np.zeros(R), "n_hits": np.zeros(R, np.int32), "mask": np.zeros(R, np.int32)}
     grads = None
@@ -155,11 +158,11 @@ def render_rays(scene, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background
 
 
 def render(scene, cams, ray_cam, px, py, Q, eps1=1e-4, k_max=2 ** 31 - 1, background=(0, 0, 0),
-           t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, sort_key=0, dl_depth=None):
+           t_near=0.0, dl_rgb=None, dl_alpha=None, threads=None, sort_key=0, dl_depth=None, eps2=None):
     """Render the listed pixels (camera index, x, y) with FP32-defined rays."""
     o, d = raygen_f32(cams, ray_cam, px, py)
     return render_rays(scene, o, d, Q, eps1, k_max, background, t_near, dl_rgb, dl_alpha, threads,
-                       sort_key=sort_key, dl_depth=dl_depth)
+                       sort_key=sort_key, dl_depth=dl_depth, eps2=eps2)
 
 
 def morton(means, bits, scales=None):

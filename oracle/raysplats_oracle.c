@@ -31,8 +31,12 @@
  *     composited;
  *   - RGB = C + T_final * background, alpha = 1 - T_final, depth = sum w_i t_key_i;
  *   - the gradient is the exact derivative of those outputs (depth included) with the hit
- *     set, order and cut point held fixed (the paper's eps2 phase is a different estimator,
- *     not this one).
+ *     set, order and cut point held fixed (grad_mode 0);
+ *   - grad_mode 1 is the paper's eps2 estimator (Sec. 3, Sec. 5): when T falls below eps1 at
+ *     hit i, the hits behind it are collected in order, without compositing, until the
+ *     product of their (1 - alpha) falls below eps2; dL/dalpha_i then uses the colour S and
+ *     alpha S_A seen behind i through those hits (plus the background through what they let
+ *     pass) instead of the background alone.  Every other gradient term is unchanged.
  */
 #include <math.h>
 #include <pthread.h>
@@ -58,6 +62,9 @@ typedef struct {
     double bg[3];    /* background colour */
     int32_t k_max;   /* at most k_max composited hits per ray */
     int32_t sort_key; /* 0: order hits by entry t1; 1: by t_m, the maximum-response parameter */
+    double eps2;      /* second threshold of the last "meaningful" Gaussian's gradient (Sec. 3) */
+    int32_t grad_mode; /* 0: exact gradient of the rendered image; 1: the eps2 estimator */
+    int32_t pad;
 } or_params;
 
 /* Ambiguity flags (per ray).  FP32 and FP64 may legitimately take a different discrete
@@ -76,6 +83,7 @@ enum {
     OR_AMB_EPS1 = 4,
     OR_AMB_TNEAR = 8,
     OR_AMB_IMPACT = 16,
+    OR_AMB_EPS2 = 256, /* a phase-2 product within 1e-4 relative of eps2 (the eps2 stop) */
     /* which alternative produced the impact (diagnostics) */
     OR_IMP_BOUNDARY = 32,
     OR_IMP_TIE = 64,
@@ -298,7 +306,7 @@ static void push_contrib(or_job* J, int64_t idx, const double v[14]) {
  * dD2/d(box) = 2 <p, do'/d(box)> - 2 tau <p, dd'/d(box)>. */
 static void ray_gradient(or_job* J, const double o[3], const double d[3], const or_hit* hits,
                          int nh, const double* alpha, const double* T, const double* gc,
-                         double ga, double gd) {
+                         double ga, double gd, const double* S_over) {
     const double* bg = J->prm->bg;
     const double Q = J->prm->Q;
     double U[3] = {bg[0], bg[1], bg[2]};
@@ -313,8 +321,12 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
         for (int ch = 0; ch < 3; ++ch) v[11 + ch] = gc[ch] * Ti * a;
         /* dL/dalpha; depth is composited like a colour channel with value t_key */
         const double tk = hits[h].t;
-        double dLda = ga * Ti * (1.0 - UA) + gd * Ti * (tk - UD);
-        for (int ch = 0; ch < 3; ++ch) dLda += gc[ch] * Ti * (c[ch] - U[ch]);
+        /* eps2 estimator: the last composited hit sees the phase-2 colour / alpha behind it */
+        const int over = S_over && h == nh - 1;
+        const double* Ub = over ? S_over : U;
+        const double UAb = over ? S_over[3] : UA;
+        double dLda = ga * Ti * (1.0 - UAb) + gd * Ti * (tk - UD);
+        for (int ch = 0; ch < 3; ++ch) dLda += gc[ch] * Ti * (c[ch] - Ub[ch]);
         for (int ch = 0; ch < 3; ++ch) U[ch] = a * c[ch] + (1.0 - a) * U[ch];
         UA = a + (1.0 - a) * UA;
         UD = a * tk + (1.0 - a) * UD;
@@ -543,6 +555,24 @@ static void* render_worker(void* arg) {
             }
         }
         if (impact > OR_IMPACT_TOL) mask |= OR_AMB_IMPACT;
+        /* 4b. eps2 estimator: phase 2 after an eps1 stop (Sec. 3) */
+        double S[4];
+        int use_S = 0;
+        if (P->grad_mode == 1 && count > 0 && prim.T < P->eps1) {
+            double T2 = 1.0;
+            S[0] = S[1] = S[2] = 0.0;
+            for (int64_t h = count; h < nh; ++h) {
+                const int64_t i = hits[h].idx;
+                const double al = J->opac[i] * exp(-0.5 * hits[h].D2);
+                for (int ch = 0; ch < 3; ++ch) S[ch] += T2 * al * J->rgb[3 * i + ch];
+                T2 *= (1.0 - al);
+                if (fabs(T2 - P->eps2) < 1e-4 * P->eps2) mask |= OR_AMB_EPS2;
+                if (T2 < P->eps2) break;
+            }
+            for (int ch = 0; ch < 3; ++ch) S[ch] += T2 * P->bg[ch];
+            S[3] = 1.0 - T2;
+            use_S = 1;
+        }
         for (int ch = 0; ch < 3; ++ch) J->out_rgb[3 * r + ch] = prim.C[ch];
         J->out_alpha[r] = 1.0 - prim.T;
         J->out_depth[r] = prim.depth;
@@ -554,7 +584,7 @@ static void* render_worker(void* arg) {
             const double* gc = J->dl_rgb + 3 * r;
             const double ga = J->dl_alpha ? J->dl_alpha[r] : 0.0;
             const double gd = J->dl_depth ? J->dl_depth[r] : 0.0;
-            ray_gradient(J, o, d, hits, (int)count, alpha, T, gc, ga, gd);
+            ray_gradient(J, o, d, hits, (int)count, alpha, T, gc, ga, gd, use_S ? S : NULL);
         }
     }
     free(hits);

@@ -498,6 +498,34 @@ def test_sort_key_changes_the_compositing_order():
     np.testing.assert_allclose(oracle.render_rays(sc, o, d, Q99, sort_key=1)["rgb"][0], small_first, atol=1e-14)
 
 
+def test_eps2_estimator_closed_forms():
+    """Sec. 3's second threshold: after the eps1 cut at hit 1, hits behind are collected until
+    the product of their (1 - alpha) drops below eps2; dL/dalpha_1 then sees their colour
+    instead of the background.  Three Gaussians on the ray through their centres (alpha =
+    opacity): with eps2 = 0.01, hit 2 (alpha 0.5) is collected and so is hit 3; with alpha_2 =
+    0.995 the product falls below eps2 at hit 2 and hit 3 is not seen."""
+    bg = np.array([0.1, 0.2, 0.3])
+    c = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    for a2, collect3 in ((0.5, True), (0.995, False)):
+        ops = [0.99995, a2, 0.7]
+        sc, perm, inv = _line_scene(ops, c)
+        o, d = [[0.0, 0.0, -3.0]], [[0.0, 0.0, 1.0]]
+        a = [float(np.float32(x)) for x in ops]
+        kw = dict(Q=Q99, eps1=1e-4, background=tuple(bg))
+        gc = np.array([[1.0, 1.0, 1.0]])
+        exact = oracle.render_rays(sc, o, d, dl_rgb=gc, **kw)
+        est = oracle.render_rays(sc, o, d, dl_rgb=gc, eps2=0.01, **kw)
+        np.testing.assert_array_equal(exact["rgb"], est["rgb"])   # the image is unchanged
+        assert exact["n_hits"][0] == 1
+        S = a[1] * c[1] + (1 - a[1]) * (a[2] * c[2] + (1 - a[2]) * bg) if collect3 else a[1] * c[1] + (1 - a[1]) * bg
+        g1 = inv[0]  # storage index of the first Gaussian along the ray
+        np.testing.assert_allclose(exact["grads"]["opacities"][g1], np.sum(c[0] - bg), atol=1e-12)
+        np.testing.assert_allclose(est["grads"]["opacities"][g1], np.sum(c[0] - S), atol=1e-12)
+        # the collected Gaussians are not composited: they receive no gradient
+        np.testing.assert_array_equal(est["grads"]["opacities"][inv[1]], 0.0)
+        np.testing.assert_array_equal(est["grads"]["rgb"][inv[2]], 0.0)
+
+
 # ----------------------------------------------------------------------------------------
 # Acceleration-structure references (plain definitions)
 # ----------------------------------------------------------------------------------------
