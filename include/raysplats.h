@@ -89,7 +89,14 @@ typedef struct {
  *               values unsupported
  *   sort_key    0: order hits by (t1, id), t1 the ellipsoid entry (Prop. 1); 1: by (t_m, id),
  *               t_m the ray parameter of the Gaussian's maximum response (Prop. 2, the chord
- *               midpoint); the hit test (D^2 <= Q, t1 >= t_near) is the same for both */
+ *               midpoint); the hit test (D^2 <= Q, t1 >= t_near) is the same for both
+ *   grad_mode   0: the adjoint is the exact derivative of the rendered outputs; 1: the paper's
+ *               eps2 estimator (Sec. 3, Sec. 5): a ray cut by eps1 after hit i goes on
+ *               collecting the hits behind i, without compositing them, until the product of
+ *               their (1 - alpha) falls below eps2, and dL/dalpha_i uses the colour and alpha
+ *               seen through them (plus the background) instead of the background alone; the
+ *               image is the same in both modes (16 B more state per ray)
+ *   eps2        the second threshold, > 0 (read when grad_mode is 1) */
 typedef struct {
     float Q;
     float eps1;
@@ -98,6 +105,8 @@ typedef struct {
     int32_t k_max;
     int32_t depth_mode;
     int32_t sort_key;
+    int32_t grad_mode;
+    float eps2;
 } rs_render_params;
 
 /* Frame outputs, device, cameras concatenated in order, each camera row major (y, x):

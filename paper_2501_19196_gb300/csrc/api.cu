@@ -212,6 +212,10 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     if (p->depth_mode != 0) return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 is implemented");
     if (p->sort_key != 0 && p->sort_key != 1)
         return set_error(RS_ERR_INVALID_ARG, "sort_key %d: must be 0 (entry t1) or 1 (t_m)", p->sort_key);
+    if (p->grad_mode != 0 && p->grad_mode != 1)
+        return set_error(RS_ERR_INVALID_ARG, "grad_mode %d: must be 0 (exact) or 1 (eps2 estimator)", p->grad_mode);
+    if (p->grad_mode == 1 && !(p->eps2 > 0.f && finite(p->eps2)))
+        return set_error(RS_ERR_INVALID_ARG, "eps2 must be finite and > 0 with grad_mode 1");
     for (int k = 0; k < 3; ++k)
         if (!finite(p->background[k])) return set_error(RS_ERR_INVALID_ARG, "background must be finite");
     if (!out || !out->rgb || !out->alpha) return set_error(RS_ERR_INVALID_ARG, "output rgb/alpha are NULL");
@@ -266,6 +270,13 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
             return st;
         }
         S->cap_pix = pix;
+    }
+    if (p->grad_mode == 1 && pix > S->cap_sS) {
+        if ((st = dmalloc(S->sS, pix))) {
+            S->cap_sS = 0;
+            return st;
+        }
+        S->cap_sS = pix;
     }
     const int64_t n_ids = pix * tune->hit_list;
     if (n_ids > S->cap_ids) {
@@ -323,6 +334,9 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
     P.n_nodes = (int32_t)std::max<int64_t>(1, g->n - 1);
     P.list_cap = tune->hit_list;
     P.sort_key = p->sort_key;
+    P.grad_mode = p->grad_mode;
+    P.eps2 = p->eps2;
+    P.sS = p->grad_mode == 1 ? S->sS : nullptr;
     P.ids = tune->hit_list > 0 ? S->ids : nullptr;
     S->P = P;
 
@@ -353,7 +367,8 @@ static rs_status render_impl(const rs_gaussians* g, const rs_accel* accel, const
         A.total_tiles = tiles;
         if (cudaMemsetAsync(S->queue, 0, sizeof(unsigned long long), s) != cudaSuccess) return cuda_check("queue reset");
         const int grid = (int)std::min<int64_t>(
-            persistent_grid_fwd(tune->kbuf, block, count, tune->traversal, A.n_top, sm_count()),
+            persistent_grid_fwd(tune->kbuf, block, count, p->grad_mode == 1 ? 2 : tune->traversal, A.n_top,
+                                sm_count()),
             (tiles + tune->block_warps - 1) / tune->block_warps);
         const cudaError_t e = launch_forward(A, tune->kbuf, true, count, tune->traversal, std::max(grid, 1),
                                              block, s);
@@ -522,7 +537,7 @@ rs_status rs_accel_destroy(rs_accel* A) {
 rs_status rs_state_destroy(rs_fwd_state* S) {
     if (!S) return RS_OK;
     cudaDeviceSynchronize();
-    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->ids, S->gtmp, S->ovf, S->queue, S->err};
+    void* ptrs[] = {S->cams_dev, S->sT, S->skey, S->sn, S->ids, S->sS, S->gtmp, S->ovf, S->queue, S->err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (S->cams_pinned) cudaFreeHost(S->cams_pinned);

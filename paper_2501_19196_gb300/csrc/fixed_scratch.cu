@@ -209,6 +209,9 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     F.P.list_cap = 0;  // forward only: no hit list
     F.P.ids = nullptr;
     F.P.sort_key = p->sort_key;
+    F.P.grad_mode = 0;  // forward only: the gradient mode does not change the image
+    F.P.eps2 = 1.f;
+    F.P.sS = nullptr;
     F.rgb = out->rgb;
     F.alpha = out->alpha;
     F.depth = out->depth;

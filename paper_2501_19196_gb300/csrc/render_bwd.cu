@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
         const int nl = n <= A.P.list_cap ? n : 0;
         float3 o, d;
         camera_ray(cam, px, py, o, d);
-        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f};
+        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f, {0.f, 0.f, 0.f, -1.f}};
         float Tf = 1.f;
         if (nl > 0) {
             g.c[0] = B.d_rgb[3 * pix];
@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
             g.c[2] = B.d_rgb[3 * pix + 2];
             g.a = B.d_alpha ? B.d_alpha[pix] : 0.f;
             g.d = DEPTH ? B.d_depth[pix] : 0.f;
+            if (A.P.grad_mode == 1) {
+                const float4 o = A.P.sS[pix];
+                g.o[0] = o.x;
+                g.o[1] = o.y;
+                g.o[2] = o.z;
+                g.o[3] = o.w;
+            }
             Tf = A.sT[pix];
         }
         if (COUNT && n > 0) ++rays;
@@ -98,7 +105,7 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
         const int nt = n > A.P.list_cap ? n : 0;  // rays the hit list cannot replay
         float3 o, d;
         camera_ray(cam, px, py, o, d);
-        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f};
+        Upstream g{{0.f, 0.f, 0.f}, 0.f, 0.f, {0.f, 0.f, 0.f, -1.f}};
         float Tf = 1.f;
         int64_t lk = -1;
         if (nt > 0) {
@@ -107,6 +114,13 @@ __global__ void __launch_bounds__(128) k_render_bwd(FwdArgs A, BwdArgs B) {
             g.c[2] = B.d_rgb[3 * pix + 2];
             g.a = B.d_alpha ? B.d_alpha[pix] : 0.f;
             g.d = DEPTH ? B.d_depth[pix] : 0.f;
+            if (A.P.grad_mode == 1) {
+                const float4 o = A.P.sS[pix];
+                g.o[0] = o.x;
+                g.o[1] = o.y;
+                g.o[2] = o.z;
+                g.o[3] = o.w;
+            }
             Tf = A.sT[pix];
             lk = A.skey[pix];
             if (COUNT) {

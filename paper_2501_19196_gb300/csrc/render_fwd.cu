@@ -6,7 +6,7 @@
 
 namespace rs {
 
-template <int K, bool PERSIST, bool COUNT, int MODE>
+template <int K, bool PERSIST, bool COUNT, int MODE, bool EPS2 = false>
 __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
     extern __shared__ float4 s_top[];
     if (MODE != 3)
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
             trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
         else if (MODE == 2)
-            trace_forward_bf<K, COUNT, 2>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
+            trace_forward_bf<K, COUNT, 2, EPS2>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
         else if (MODE == 1)
             trace_forward_packet<K, COUNT>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
@@ -136,7 +136,10 @@ int persistent_grid_fwd(int K, int block, bool count, int mode, int n_top, int s
 template <int K, bool PERSIST, bool COUNT>
 static void launch_fwd_mode(const FwdArgs& A, int mode, int grid, int block, cudaStream_t st) {
     const size_t sm = smem_bytes(A.n_top);
-    if (mode == 3) k_render_fwd<K, PERSIST, COUNT, 3><<<grid, block, 0, st>>>(A);
+    // the eps2 estimator's phase 2 is built into the best-first traversal only (every traversal
+    // order gives the same result, so the order is a free choice)
+    if (A.P.grad_mode == 1) k_render_fwd<K, PERSIST, COUNT, 2, true><<<grid, block, sm, st>>>(A);
+    else if (mode == 3) k_render_fwd<K, PERSIST, COUNT, 3><<<grid, block, 0, st>>>(A);
     else if (mode == 2) k_render_fwd<K, PERSIST, COUNT, 2><<<grid, block, sm, st>>>(A);
     else if (mode == 1) k_render_fwd<K, PERSIST, COUNT, 1><<<grid, block, sm, st>>>(A);
     else k_render_fwd<K, PERSIST, COUNT, 0><<<grid, block, sm, st>>>(A);

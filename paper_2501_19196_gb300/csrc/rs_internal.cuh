@@ -60,6 +60,10 @@ struct TraceParams {
     int32_t list_cap;      // hit list: ids of the first list_cap composited hits per ray (0: none)
     int* ids;              // hit list storage, list_cap ints per pixel (pixel-major rows)
     int32_t sort_key;      // hits ordered by 0: entry t1, 1: t_m (maximum response)
+    int32_t grad_mode;     // 0: exact gradient; 1: the eps2 estimator for the last meaningful hit
+    float eps2;            // second threshold (grad_mode 1)
+    float4* sS;            // grad_mode 1: per pixel, colour and alpha behind the last composited
+                           // hit through the phase-2 hits (.w < 0: no phase 2)
 };
 
 // (t1, sorted id) packed into one ordered 64-bit key; t1 >= 0 so its bit pattern orders as

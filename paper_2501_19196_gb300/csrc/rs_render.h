@@ -76,6 +76,8 @@ struct rs_fwd_state {
     int* sn = nullptr;
     int* ids = nullptr;                 // hit lists (hit_list ids per pixel)
     int64_t cap_ids = 0;
+    float4* sS = nullptr;               // eps2 estimator: colour / alpha behind the last hit
+    int64_t cap_sS = 0;
     float4* gtmp = nullptr;
     int* ovf = nullptr;                 // overflow tile list of the adjoint
     int64_t cap_ovf = 0;

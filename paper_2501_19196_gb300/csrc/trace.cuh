@@ -305,12 +305,22 @@ struct Counters {
 // to replay and the colour / alpha / depth composited behind it (App. A.4-A.5).
 struct Adjoint {
     float Tn, U0, U1, U2, UA, UD;
+    float O0, O1, O2, OA;  // eps2 estimator: colour / alpha behind the first replayed hit (OA < 0: none)
 };
 
-// Upstream gradient of one ray: dL/d(rgb), dL/d(alpha), dL/d(depth).
+
+
+// Upstream gradient of one ray: dL/d(rgb), dL/d(alpha), dL/d(depth); and, for the eps2
+// estimator, the colour / alpha behind its last composited hit (o[3] < 0: none).
 struct Upstream {
     float c[3], a, d;
+    float o[4];
 };
+
+// Start the back-to-front replay of one ray.
+__device__ __forceinline__ Adjoint adjoint_start(const TraceParams& P, float T_final, const Upstream& g) {
+    return Adjoint{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f, g.o[0], g.o[1], g.o[2], g.o[3]};
+}
 
 // The adjoint of one composited hit (sorted Gaussian j), given the hits behind it: recovers
 // T_i = T_{i+1} / (1 - alpha_i), forms dL/dalpha_i = T_i (sum_ch g_ch (c_ch - U_ch) +
@@ -338,7 +348,12 @@ __device__ __forceinline__ void adjoint_hit(const float4* __restrict__ rec, int 
     const float om = __fsub_rn(1.f, a);
     const float Ti = __fdiv_rn(s.Tn, om);
     const float w = Ti * a;
-    float dLda = Ti * (g.c[0] * (sh.y - s.U0) + g.c[1] * (sh.z - s.U1) + g.c[2] * (sh.w - s.U2) + g.a * (1.f - s.UA));
+    // the eps2 estimator replaces what the first replayed (last composited) hit sees behind it
+    const bool over = s.OA >= 0.f;
+    const float B0 = over ? s.O0 : s.U0, B1 = over ? s.O1 : s.U1, B2 = over ? s.O2 : s.U2;
+    const float BA = over ? s.OA : s.UA;
+    s.OA = -1.f;
+    float dLda = Ti * (g.c[0] * (sh.y - B0) + g.c[1] * (sh.z - B1) + g.c[2] * (sh.w - B2) + g.a * (1.f - BA));
     if (DEPTH) dLda = fmaf(Ti, g.d * (tk - s.UD), dLda);
     s.U0 = fmaf(a, sh.y, om * s.U0);
     s.U1 = fmaf(a, sh.z, om * s.U1);
@@ -582,7 +597,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
     const float NINF = __int_as_float(0xff800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;  // exclusive upper bound
-    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
+    Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits;
     int passes = 0;
     int st_node[kStackSize];
@@ -795,7 +810,7 @@ __device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int
 template <bool COUNT, bool DEPTH>
 __device__ __forceinline__ void replay_list(const float4* __restrict__ rec, const TraceParams& P, int64_t pix,
                                             const float3 o, const float3 d, float T_final, int n, const Upstream& g, float4* __restrict__ gtmp, Counters& cnt, int* err) {
-    Adjoint s{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
+    Adjoint s = adjoint_start(P, T_final, g);
     const int* row = P.ids + (n > 0 ? pix * P.list_cap : 0);
     int k = n > 0 ? n : 0;
     while (__any_sync(0xffffffffu, k > 0)) {
@@ -1021,7 +1036,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
     const float NINF = __int_as_float(0xff800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
+    Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     int st_node[kStackSize];
@@ -1328,7 +1343,11 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
     return __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(v)));
 }
 
-template <int K, bool COUNT, int W>
+// EPS2: the eps2 estimator's phase 2 (Sec. 3): after the eps1 cut, the ray goes on collecting
+// hits in order without compositing them, accumulating the colour S and transmittance T2 seen
+// behind its last composited hit until T2 < eps2; (S + T2 background, 1 - T2) is stored per
+// pixel for the adjoint.
+template <int K, bool COUNT, int W, bool EPS2 = false>
 __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                  const TraceParams& P, int64_t pix, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
@@ -1344,6 +1363,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     count = 0;
     last_key = -1;
     int64_t lo_key = -1;
+    int64_t lp_key = -1;  // last key composited or (phase 2) collected
+    bool ph2 = false;
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f, T2 = 1.f;
     bool done = !valid;
     int passes = 0;
     while (__any_sync(FULL, !done)) {
@@ -1369,6 +1391,17 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                  P.t_near, hc);
             const float4 sh = __ldg(rec + 4 * j + 3);
             const float a = response_alpha(sh.x, hc.D2);
+            if (EPS2 && ph2) {  // phase 2: collect, do not composite
+                const float w2 = __fmul_rn(T2, a);
+                S0 = fmaf(w2, sh.y, S0);
+                S1 = fmaf(w2, sh.z, S1);
+                S2 = fmaf(w2, sh.w, S2);
+                T2 = __fmul_rn(T2, __fsub_rn(1.f, a));
+                lp_key = key;
+                if (T2 < P.eps2) done = true;
+                kbuf_pop_warp<K>(keys, nk, kEmptyKey, __activemask());
+                return;
+            }
             const float w = __fmul_rn(T, a);
             C0 = fmaf(w, sh.y, C0);
             C1 = fmaf(w, sh.z, C1);
@@ -1378,8 +1411,10 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             if (count < P.list_cap) P.ids[pix * P.list_cap + count] = j;  // for the adjoint's list replay
             ++count;
             last_key = key;
+            lp_key = key;
             if (COUNT) cnt.hits++;
-            if (T < eps || count >= P.k_max) done = true;
+            if (EPS2 && T < eps) ph2 = true;
+            else if (T < eps || count >= P.k_max) done = true;
             kbuf_pop_warp<K>(keys, nk, kEmptyKey, __activemask());
         };
         auto drop_cap = [&](float e) {  // a node with packet entry e was dropped for this pass
@@ -1520,9 +1555,12 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         }
         if (active && !done) {
             if (cap == kEmptyKey) done = true;
-            else lo_key = last_key;
+            else lo_key = EPS2 ? lp_key : last_key;
         }
     }
+    if (EPS2 && valid)
+        P.sS[pix] = ph2 ? make_float4(fmaf(T2, P.bg[0], S0), fmaf(T2, P.bg[1], S1), fmaf(T2, P.bg[2], S2), 1.f - T2)
+                        : make_float4(0.f, 0.f, 0.f, -1.f);
 }
 
 template <int K, bool COUNT, int W, bool DEPTH>
@@ -1536,7 +1574,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
     const float INF = __int_as_float(0x7f800000);
     constexpr int64_t kFloorJ = 0x7fffffff;
     int64_t hi_key = last_key + 1;
-    Adjoint adj{T_final, P.bg[0], P.bg[1], P.bg[2], 0.f, 0.f};
+    Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits > 0 ? n_hits : 0;
     int passes = 0;
     while (__any_sync(FULL, remaining > 0)) {

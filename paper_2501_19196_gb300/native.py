@@ -28,7 +28,7 @@ class RsCamera(ctypes.Structure):
 
 class RsRenderParams(ctypes.Structure):
     _fields_ = [("Q", f32), ("eps1", f32), ("t_near", f32), ("background", f32 * 3), ("k_max", i32),
-                ("depth_mode", i32), ("sort_key", i32)]
+                ("depth_mode", i32), ("sort_key", i32), ("grad_mode", i32), ("eps2", f32)]
 
 
 class RsFrame(ctypes.Structure):

@@ -30,12 +30,14 @@ class RenderParams:
     background: tuple = (0.0, 0.0, 0.0)
     k_max: int = 2 ** 31 - 1
     sort_key: int = 0  # 0: order hits by entry t1; 1: by t_m (maximum response)
+    eps2: float | None = None  # set: the adjoint uses the paper's eps2 estimator
 
     def to_c(self) -> native.RsRenderParams:
         p = native.RsRenderParams()
         p.Q, p.eps1, p.t_near = float(self.Q), float(self.eps1), float(self.t_near)
         p.background[:] = [float(x) for x in self.background]
         p.k_max, p.depth_mode, p.sort_key = int(self.k_max), 0, int(self.sort_key)
+        p.grad_mode, p.eps2 = (0, 1.0) if self.eps2 is None else (1, float(self.eps2))
         return p
 
 

@@ -15,10 +15,10 @@ def to_dev(scene, device="cuda"):
     return f(scene.means), f(scene.quats), f(scene.scales), f(scene.opacities), f(scene.rgb)
 
 
-def params(Q=None, eps1=1e-4, k_max=2 ** 31 - 1, background=(0.0, 0.0, 0.0), t_near=0.0, sort_key=0):
+def params(Q=None, eps1=1e-4, k_max=2 ** 31 - 1, background=(0.0, 0.0, 0.0), t_near=0.0, sort_key=0, eps2=None):
     from paper_2501_19196_gb300 import RenderParams
     return RenderParams(Q=scenes.default_Q() if Q is None else Q, eps1=eps1, t_near=t_near,
-                        background=tuple(background), k_max=k_max, sort_key=sort_key)
+                        background=tuple(background), k_max=k_max, sort_key=sort_key, eps2=eps2)
 
 
 def gpu_render(scene, cams, prm, tune=None, renderer=None, keep=False):
@@ -44,7 +44,8 @@ def pixel_index(cams, cam, px, py):
 
 def oracle_pixels(scene, cams, cam, px, py, prm, dl_rgb=None, dl_alpha=None, dl_depth=None):
     return oracle.render(scene, cams, cam, px, py, prm.Q, prm.eps1, prm.k_max, prm.background, prm.t_near,
-                         dl_rgb=dl_rgb, dl_alpha=dl_alpha, sort_key=prm.sort_key, dl_depth=dl_depth)
+                         dl_rgb=dl_rgb, dl_alpha=dl_alpha, sort_key=prm.sort_key, dl_depth=dl_depth,
+                         eps2=prm.eps2)
 
 
 def compare_image(gpu, ora, idx, tol=TOL_RGB, max_masked=0.02, label=""):

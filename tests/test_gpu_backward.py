@@ -81,6 +81,23 @@ def test_depth_gradients_tiny_scenes(seed, sort_key):
         assert max(errs.values()) < TOL_GRAD, (kw, tune, errs)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_eps2_estimator_gradients(seed):
+    """The paper's eps2 estimator (Sec. 3): rays cut by eps1 (0.05 / 0.2 here, so that many
+    are) give their last composited hit dL/dalpha from the phase-2 hits behind it; through the
+    hit-list replay and through every re-traversing adjoint, with and without depth."""
+    from paper_2501_19196_gb300 import native
+    sc = scenes.random_tiny_scene(340 + seed, n=60, flat_frac=0.3 if seed % 2 else 0.0)
+    cams = scenes.concat_cameras([scenes.look_at_camera((0.4, 0.3, -3.2), (0, 0, 0), 21, 17, 55.0),
+                                  scenes.look_at_camera((-3.0, 0.5, 0.7), (0.1, 0, 0), 16, 16, 45.0)])
+    for kw, tune, depth in ((dict(eps1=0.05, eps2=0.01), dict(), False),
+                            (dict(eps1=0.2, eps2=0.05, background=(0.3, 0.2, 1.0)), dict(hit_list=0), True),
+                            (dict(eps1=0.2, eps2=0.001), dict(hit_list=0, traversal=0), False),
+                            (dict(eps1=0.05, eps2=0.01, sort_key=1), dict(hit_list=2, traversal=1), True)):
+        errs, bad = _grad_case(sc, cams, params(**kw), tune=native.default_tune(**tune), seed=seed, with_depth=depth)
+        assert max(errs.values()) < TOL_GRAD, (kw, tune, errs)
+
+
 def test_gradients_workload_1k_full_frame():
     wl = scenes.workload(1)
     errs, bad = _grad_case(wl.scene, wl.cams, params(eps1=wl.eps1, background=wl.background))

@@ -225,6 +225,10 @@ def test_tunables_and_launch_modes_bit_identical():
                                   scenes.look_at_camera((-2.0, -2.5, 1.5), (0, 0, 0), 33, 70, 60)])
     prm = params(eps1=1e-3, background=(1, 1, 1))
     ref = gpu_render(sc, cams, prm, tune=native.default_tune())
+    # the eps2 estimator changes the adjoint only: the image is the same bits
+    est = gpu_render(sc, cams, params(eps1=1e-3, background=(1, 1, 1), eps2=0.01), tune=native.default_tune(traversal=3))
+    for k in ("rgb", "alpha", "depth"):
+        np.testing.assert_array_equal(est[k], ref[k], err_msg="eps2 " + k)
     prm1 = params(eps1=1e-3, background=(1, 1, 1), sort_key=1)
     ref1 = gpu_render(sc, cams, prm1, tune=native.default_tune())
     for kw in (dict(traversal=0), dict(traversal=1), dict(traversal=3), dict(kbuf=8, leaf_size=1),
