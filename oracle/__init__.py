@@ -59,6 +59,8 @@ def lib():
         L.or_radix_tree.argtypes = [i64, P, P, P, P]
         L.or_chi2_3_quantile.restype = ctypes.c_double
         L.or_chi2_3_quantile.argtypes = [ctypes.c_double]
+        L.or_render_scene.restype = ctypes.c_int
+        L.or_render_scene.argtypes = [i64, P, P, P, P, P, P, i64, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]
         _LIB = L
     return _LIB
 
@@ -201,3 +203,54 @@ def radix_tree(sorted_codes):
 
 def chi2_3_quantile(p):
     return float(lib().or_chi2_3_quantile(float(p)))
+
+
+AMB_SURFACE = 512  # a triangle decision within FP32 rounding (scene renders)
+
+
+class OrScene(ctypes.Structure):
+    _fields_ = [("n_tri", ctypes.c_int64), ("verts", ctypes.c_void_p), ("mat", ctypes.c_void_p),
+                ("albedo", ctypes.c_void_p), ("light", ctypes.c_float * 3), ("max_bounces", ctypes.c_int32),
+                ("eps_off", ctypes.c_float)]
+
+
+def render_scene(scene, mesh, ray_o, ray_d, Q, eps1=1e-4, k_max=2 ** 31 - 1, background=(0, 0, 0), t_near=0.0,
+                 dl_rgb=None, dl_alpha=None, dl_depth=None, params64=None):
+    """Render FP32 rays through Gaussians and a triangle mesh (mirror / diffuse, one point light).
+    mesh: dict with verts (T, 3, 3) float32, mat (T,) int32 (0 mirror, 1 diffuse), albedo (T, 3),
+    light (3,), max_bounces, eps_off.  Returns rgb, alpha, depth, n_hits, mask and, with dl_rgb,
+    the float64 gradients w.r.t. the Gaussian parameters."""
+    src = params64 if params64 is not None else {
+        "means": scene.means, "quats": scene.quats, "scales": scene.scales,
+        "opacities": scene.opacities, "rgb": scene.rgb}
+    means, quats, scales = (_c(src[k], np.float64) for k in ("means", "quats", "scales"))
+    opac, rgb = _c(src["opacities"], np.float64), _c(src["rgb"], np.float64)
+    n = means.shape[0]
+    ray_o, ray_d = _c(ray_o, np.float32), _c(ray_d, np.float32)
+    R = ray_o.shape[0]
+    verts = _c(mesh["verts"], np.float32).reshape(-1, 9)
+    mat = _c(mesh["mat"], np.int32)
+    alb = _c(mesh["albedo"], np.float32).reshape(-1, 3)
+    S = OrScene(verts.shape[0], _p(verts), _p(mat), _p(alb), (ctypes.c_float * 3)(*mesh["light"]),
+                int(mesh["max_bounces"]), float(mesh["eps_off"]))
+    prm = OrParams(float(Q), float(eps1), float(t_near), (ctypes.c_double * 3)(*background), int(k_max), 0,
+                   0.0, 0, 0)
+    out = {"rgb": np.zeros((R, 3)), "alpha": np.zeros(R), "depth": np.zeros(R),
+           "n_hits": np.zeros(R, np.int32), "mask": np.zeros(R, np.int32)}
+    grads = None
+    if dl_rgb is not None:
+        dl_rgb = _c(dl_rgb, np.float64)
+        dl_alpha = None if dl_alpha is None else _c(dl_alpha, np.float64)
+        dl_depth = None if dl_depth is None else _c(dl_depth, np.float64)
+        grads = {"means": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "scales": np.zeros((n, 3)),
+                 "opacities": np.zeros(n), "rgb": np.zeros((n, 3))}
+    rc = lib().or_render_scene(
+        n, _p(means), _p(quats), _p(scales), _p(opac), _p(rgb), ctypes.byref(S), R, _p(ray_o), _p(ray_d),
+        ctypes.byref(prm), _p(out["rgb"]), _p(out["alpha"]), _p(out["depth"]), _p(out["n_hits"]), _p(out["mask"]),
+        _p(dl_rgb), _p(dl_alpha), _p(dl_depth),
+        *(_p(grads[k]) if grads else None for k in ("means", "quats", "scales", "opacities", "rgb")))
+    if rc != 0:
+        raise MemoryError("oracle scene render failed")
+    if grads is not None:
+        out["grads"] = grads
+    return out

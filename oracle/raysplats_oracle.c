@@ -296,6 +296,78 @@ static void push_contrib(or_job* J, int64_t idx, const double v[14]) {
     J->n_contrib++;
 }
 
+/* App. A.6 chain from dL/dalpha (and dL/dt_key for the depth output) of hit Gaussian i on the
+ * ray (o, d) to its mean, quaternion, scales and opacity: fills v[0..10]. */
+static void param_chain(const or_job* J, const double o[3], const double d[3], int64_t i, double a,
+                        double dLda, double dLdt, double v[14]) {
+    const double Q = J->prm->Q;
+    const double* m = J->means + 3 * i;
+    const double* q = J->quats + 4 * i;
+    const double* s = J->scales + 3 * i;
+    const double* M = J->M + 9 * i;
+    or_geom g;
+    ray_gauss(o, d, m, M, J->prm->Q, &g);
+    const double e = exp(-0.5 * g.D2);
+    v[10] = dLda * e;                         /* d opacity */
+    const double dLdD2 = -0.5 * a * dLda;     /* alpha = opacity exp(-D2/2) */
+    /* t_key as a function of (o', d'): t_m = -tau = -b/a and t1 = t_m - r with
+     * r = sqrt((Q - D2)/a), so
+     *   dt_m = -db/a + tau da/a,  dt1 = dt_m + dD2/(2 r a) + (Q - D2) da/(2 r a^2),
+     * with da = 2<d', dd'>, db = <do', d'> + <o', dd'> and dD2 as below. */
+    const int use_tm = J->prm->sort_key == 1;
+    const double rr = sqrt(fmax(Q - g.D2, 0.0) / g.a);
+    /* dD2/dbox = 2<p, do'> - 2 tau <p, dd'> */
+    double om[3] = {o[0] - m[0], o[1] - m[1], o[2] - m[2]};
+    /* means: do'/dm_x = -M e_x, dd'/dm_x = 0 */
+    for (int x = 0; x < 3; ++x) {
+        double dop[3] = {-M[x], -M[3 + x], -M[6 + x]};
+        double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]);
+        v[x] = dLdD2 * dD2;
+        if (dLdt != 0.0) {
+            const double db = dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2];
+            const double dtm = -db / g.a; /* da = 0 */
+            v[x] += dLdt * (use_tm ? dtm : dtm + dD2 / (2.0 * rr * g.a));
+        }
+    }
+    /* scales: do'/ds_k = -(1/s_k) o'_k e_k, dd'/ds_k = -(1/s_k) d'_k e_k */
+    for (int k = 0; k < 3; ++k) {
+        double dD2 = 2.0 * g.p[k] * (-g.op[k] / s[k]) - 2.0 * g.tau * g.p[k] * (-g.dp[k] / s[k]);
+        v[7 + k] = dLdD2 * dD2;
+        if (dLdt != 0.0) {
+            const double dop_k = -g.op[k] / s[k], ddp_k = -g.dp[k] / s[k];
+            const double da = 2.0 * g.dp[k] * ddp_k;
+            const double db = dop_k * g.dp[k] + g.op[k] * ddp_k;
+            const double dtm = -db / g.a + g.tau * da / g.a;
+            const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
+            v[7 + k] += dLdt * (use_tm ? dtm : dt1);
+        }
+    }
+    /* quaternion: do'/dq_x = S^-1 (dR/dq_x)^T (o - m), dd'/dq_x = S^-1 (dR/dq_x)^T d */
+    double dR[4][9];
+    quat_drot(q, dR);
+    for (int x = 0; x < 4; ++x) {
+        double dop[3], ddp[3];
+        for (int k = 0; k < 3; ++k) {
+            /* row k of (dR)^T is column k of dR */
+            double ro = dR[x][k] * om[0] + dR[x][3 + k] * om[1] + dR[x][6 + k] * om[2];
+            double rd = dR[x][k] * d[0] + dR[x][3 + k] * d[1] + dR[x][6 + k] * d[2];
+            dop[k] = ro / s[k];
+            ddp[k] = rd / s[k];
+        }
+        double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]) -
+                     2.0 * g.tau * (g.p[0] * ddp[0] + g.p[1] * ddp[1] + g.p[2] * ddp[2]);
+        v[3 + x] = dLdD2 * dD2;
+        if (dLdt != 0.0) {
+            const double da = 2.0 * (g.dp[0] * ddp[0] + g.dp[1] * ddp[1] + g.dp[2] * ddp[2]);
+            const double db = (dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2]) +
+                              (g.op[0] * ddp[0] + g.op[1] * ddp[1] + g.op[2] * ddp[2]);
+            const double dtm = -db / g.a + g.tau * da / g.a;
+            const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
+            v[3 + x] += dLdt * (use_tm ? dtm : dt1);
+        }
+    }
+}
+
 /* Gradient of one ray's outputs (rgb, alpha) w.r.t. the parameters of its composited hits.
  * App. A.3: dI/dc_i = alpha_i T_i, dI/d(box) = dI/dalpha_i dalpha_i/d(box).
  * dI/dalpha_i is evaluated division-free, back to front: with U_n = background and
@@ -331,72 +403,7 @@ static void ray_gradient(or_job* J, const double o[3], const double d[3], const 
         UA = a + (1.0 - a) * UA;
         UD = a * tk + (1.0 - a) * UD;
         const double dLdt = gd * Ti * a; /* depth = sum w_i t_key_i, w_i = T_i alpha_i */
-        /* geometry */
-        const double* m = J->means + 3 * i;
-        const double* q = J->quats + 4 * i;
-        const double* s = J->scales + 3 * i;
-        const double* M = J->M + 9 * i;
-        or_geom g;
-        ray_gauss(o, d, m, M, J->prm->Q, &g);
-        const double e = exp(-0.5 * g.D2);
-        v[10] = dLda * e;                         /* d opacity */
-        const double dLdD2 = -0.5 * a * dLda;     /* alpha = opacity exp(-D2/2) */
-        /* t_key as a function of (o', d'): t_m = -tau = -b/a and t1 = t_m - r with
-         * r = sqrt((Q - D2)/a), so
-         *   dt_m = -db/a + tau da/a,  dt1 = dt_m + dD2/(2 r a) + (Q - D2) da/(2 r a^2),
-         * with da = 2<d', dd'>, db = <do', d'> + <o', dd'> and dD2 as below. */
-        const int use_tm = J->prm->sort_key == 1;
-        const double rr = sqrt(fmax(Q - g.D2, 0.0) / g.a);
-        /* dD2/dbox = 2<p, do'> - 2 tau <p, dd'> */
-        double om[3] = {o[0] - m[0], o[1] - m[1], o[2] - m[2]};
-        /* means: do'/dm_x = -M e_x, dd'/dm_x = 0 */
-        for (int x = 0; x < 3; ++x) {
-            double dop[3] = {-M[x], -M[3 + x], -M[6 + x]};
-            double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]);
-            v[x] = dLdD2 * dD2;
-            if (dLdt != 0.0) {
-                const double db = dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2];
-                const double dtm = -db / g.a; /* da = 0 */
-                v[x] += dLdt * (use_tm ? dtm : dtm + dD2 / (2.0 * rr * g.a));
-            }
-        }
-        /* scales: do'/ds_k = -(1/s_k) o'_k e_k, dd'/ds_k = -(1/s_k) d'_k e_k */
-        for (int k = 0; k < 3; ++k) {
-            double dD2 = 2.0 * g.p[k] * (-g.op[k] / s[k]) - 2.0 * g.tau * g.p[k] * (-g.dp[k] / s[k]);
-            v[7 + k] = dLdD2 * dD2;
-            if (dLdt != 0.0) {
-                const double dop_k = -g.op[k] / s[k], ddp_k = -g.dp[k] / s[k];
-                const double da = 2.0 * g.dp[k] * ddp_k;
-                const double db = dop_k * g.dp[k] + g.op[k] * ddp_k;
-                const double dtm = -db / g.a + g.tau * da / g.a;
-                const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
-                v[7 + k] += dLdt * (use_tm ? dtm : dt1);
-            }
-        }
-        /* quaternion: do'/dq_x = S^-1 (dR/dq_x)^T (o - m), dd'/dq_x = S^-1 (dR/dq_x)^T d */
-        double dR[4][9];
-        quat_drot(q, dR);
-        for (int x = 0; x < 4; ++x) {
-            double dop[3], ddp[3];
-            for (int k = 0; k < 3; ++k) {
-                /* row k of (dR)^T is column k of dR */
-                double ro = dR[x][k] * om[0] + dR[x][3 + k] * om[1] + dR[x][6 + k] * om[2];
-                double rd = dR[x][k] * d[0] + dR[x][3 + k] * d[1] + dR[x][6 + k] * d[2];
-                dop[k] = ro / s[k];
-                ddp[k] = rd / s[k];
-            }
-            double dD2 = 2.0 * (g.p[0] * dop[0] + g.p[1] * dop[1] + g.p[2] * dop[2]) -
-                         2.0 * g.tau * (g.p[0] * ddp[0] + g.p[1] * ddp[1] + g.p[2] * ddp[2]);
-            v[3 + x] = dLdD2 * dD2;
-            if (dLdt != 0.0) {
-                const double da = 2.0 * (g.dp[0] * ddp[0] + g.dp[1] * ddp[1] + g.dp[2] * ddp[2]);
-                const double db = (dop[0] * g.dp[0] + dop[1] * g.dp[1] + dop[2] * g.dp[2]) +
-                                  (g.op[0] * ddp[0] + g.op[1] * ddp[1] + g.op[2] * ddp[2]);
-                const double dtm = -db / g.a + g.tau * da / g.a;
-                const double dt1 = dtm + dD2 / (2.0 * rr * g.a) + (Q - g.D2) * da / (2.0 * rr * g.a * g.a);
-                v[3 + x] += dLdt * (use_tm ? dtm : dt1);
-            }
-        }
+        param_chain(J, o, d, i, a, dLda, dLdt, v);
         push_contrib(J, i, v);
     }
 }
@@ -814,4 +821,306 @@ double or_chi2_3_quantile(double p) {
         if (F < p) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Scenes with triangles: a mirror mesh, diffuse surfaces, one point light (the paper's    */
+/* mesh / mirror / shadow demonstrations, Sec. 1 and Fig. 1; the paper gives no algorithm, */
+/* so the rules below are this renderer's own and stated in full).                        */
+/*                                                                                        */
+/*   A ray runs in segments.  In each, Gaussians whose entry t1 lies in [t_min, t_tri)    */
+/*   are composited in (t1, index) order with the eps1 cut and k_max (counted over the    */
+/*   whole ray), t_tri being the nearest triangle.  Then, unless the ray was cut:         */
+/*     - no triangle: the environment term is the background;                              */
+/*     - diffuse triangle (albedo a): the term is a * T_s, T_s the transmittance of a     */
+/*       shadow ray from the hit point to the light: the product of (1 - alpha) over the   */
+/*       Gaussians it hits (entry in [eps_off, distance)), 0 if a triangle blocks it;      */
+/*     - mirror triangle: the ray reflects and continues (at most max_bounces times; past  */
+/*       that the term is 0).                                                              */
+/*   A ray cut by eps1 or k_max takes the term of the segment it stopped in (a mirror      */
+/*   gives 0).  RGB = sum of composited colours + T_final * term, alpha = 1 - T_final,     */
+/*   depth = sum of w_i t1_i over the first segment.                                       */
+/*   Triangle hits, reflected rays and shadow rays follow fixed FP32 operation sequences   */
+/*   (as camera rays do) so that both implementations take the same surface decisions;     */
+/*   the Gaussian arithmetic along those rays is FP64.  The gradient is the exact          */
+/*   derivative w.r.t. the Gaussian parameters (the mesh and the light are fixed).         */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_tri;
+    const float* verts;    /* 9 per triangle: v0, v1, v2 */
+    const int32_t* mat;    /* 0: mirror, 1: diffuse */
+    const float* albedo;   /* 3 per triangle (diffuse) */
+    float light[3];
+    int32_t max_bounces;
+    float eps_off;         /* start of reflected and shadow rays along their direction */
+} or_scene;
+
+#define OR_AMB_SURFACE 512 /* a triangle decision within FP32 rounding (edge, tie, t_min) */
+
+/* Moller-Trumbore in a fixed FP32 sequence; returns 1 and (t, u, v) when tmin < t < tmax. */
+static int tri_hit_f32(const float o[3], const float d[3], const float* v, float tmin, float tmax, float* t_out,
+                       float* u_out, float* v_out) {
+    const float e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+    const float e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    const float p[3] = {d[1] * e2[2] - d[2] * e2[1], d[2] * e2[0] - d[0] * e2[2], d[0] * e2[1] - d[1] * e2[0]};
+    const float det = (e1[0] * p[0] + e1[1] * p[1]) + e1[2] * p[2];
+    if (fabsf(det) < 1e-12f) return 0;
+    const float inv = 1.0f / det;
+    const float s[3] = {o[0] - v[0], o[1] - v[1], o[2] - v[2]};
+    const float u = ((s[0] * p[0] + s[1] * p[1]) + s[2] * p[2]) * inv;
+    if (u < 0.0f || u > 1.0f) return 0;
+    const float q[3] = {s[1] * e1[2] - s[2] * e1[1], s[2] * e1[0] - s[0] * e1[2], s[0] * e1[1] - s[1] * e1[0]};
+    const float w = ((d[0] * q[0] + d[1] * q[1]) + d[2] * q[2]) * inv;
+    if (w < 0.0f || u + w > 1.0f) return 0;
+    const float t = ((e2[0] * q[0] + e2[1] * q[1]) + e2[2] * q[2]) * inv;
+    if (!(t > tmin && t < tmax)) return 0;
+    *t_out = t;
+    *u_out = u;
+    *v_out = w;
+    return 1;
+}
+
+/* nearest triangle (smallest t, then smallest index) in (tmin, tmax); -1 if none */
+static int64_t nearest_tri(const or_scene* S, const float o[3], const float d[3], float tmin, float tmax, float* t,
+                           int32_t* mask) {
+    int64_t best = -1;
+    float bt = tmax, bu = 0.f, bv = 0.f;
+    for (int64_t k = 0; k < S->n_tri; ++k) {
+        float tt, uu, vv;
+        if (tri_hit_f32(o, d, S->verts + 9 * k, tmin, bt, &tt, &uu, &vv) && (tt < bt || best < 0)) {
+            best = k;
+            bt = tt;
+            bu = uu;
+            bv = vv;
+        }
+    }
+    if (best >= 0) {
+        const float band = 1e-5f;
+        if (bu < band || bv < band || 1.0f - bu - bv < band || bt < tmin * 1.001f + 1e-6f) *mask |= OR_AMB_SURFACE;
+        /* a second triangle at nearly the same t */
+        for (int64_t k = 0; k < S->n_tri; ++k) {
+            float tt, uu, vv;
+            if (k != best && tri_hit_f32(o, d, S->verts + 9 * k, tmin, tmax, &tt, &uu, &vv) &&
+                fabsf(tt - bt) < 1e-5f * fmaxf(1.0f, bt))
+                *mask |= OR_AMB_SURFACE;
+        }
+    }
+    *t = bt;
+    return best;
+}
+
+/* fixed FP32 sequences: hit point, unit normal, reflected direction, shadow ray */
+static void reflect_f32(const float o[3], const float d[3], float t, const float* v, float P[3], float dr[3]) {
+    const float e1[3] = {v[3] - v[0], v[4] - v[1], v[5] - v[2]};
+    const float e2[3] = {v[6] - v[0], v[7] - v[1], v[8] - v[2]};
+    float n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const float nl = sqrtf((n[0] * n[0] + n[1] * n[1]) + n[2] * n[2]);
+    for (int k = 0; k < 3; ++k) n[k] = n[k] / nl;
+    const float dn = (d[0] * n[0] + d[1] * n[1]) + d[2] * n[2];
+    const float k2 = 2.0f * dn;
+    float r[3];
+    for (int k = 0; k < 3; ++k) {
+        P[k] = o[k] + t * d[k];
+        r[k] = d[k] - k2 * n[k];
+    }
+    const float rl = sqrtf((r[0] * r[0] + r[1] * r[1]) + r[2] * r[2]);
+    for (int k = 0; k < 3; ++k) dr[k] = r[k] / rl;
+}
+
+static void shadow_ray_f32(const float P[3], const float L[3], float dir[3], float* dist) {
+    const float w[3] = {L[0] - P[0], L[1] - P[1], L[2] - P[2]};
+    const float dl = sqrtf((w[0] * w[0] + w[1] * w[1]) + w[2] * w[2]);
+    for (int k = 0; k < 3; ++k) dir[k] = w[k] / dl;
+    *dist = dl;
+}
+
+typedef struct {
+    int64_t idx;
+    int32_t seg;
+    double t, D2;
+} or_shit;
+
+static int shit_cmp(const void* x, const void* y) {
+    const or_shit* a = (const or_shit*)x;
+    const or_shit* b = (const or_shit*)y;
+    if (a->t < b->t) return -1;
+    if (a->t > b->t) return 1;
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+/* Gaussians hit by the ray (o, d) with entry in [tmin, tmax), appended to `out`; flags the
+ * boundary / t_min / t_max decisions that FP32 may take differently */
+static int64_t gather_hits(const or_job* J, const float of[3], const float df[3], double tmin, double tmax, int32_t seg,
+                           or_shit* out, int32_t* mask) {
+    const double o[3] = {of[0], of[1], of[2]}, d[3] = {df[0], df[1], df[2]};
+    const double Q = J->prm->Q;
+    int64_t nh = 0;
+    for (int64_t i = 0; i < J->n; ++i) {
+        or_geom g;
+        ray_gauss(o, d, J->means + 3 * i, J->M + 9 * i, Q, &g);
+        const double band = OR_TIE_REL * fmax(1.0, fabs(g.t1));
+        if (fabs(Q - g.D2) < OR_BOUNDARY_REL * Q && g.t1 >= tmin - band && g.t1 < tmax + band) *mask |= OR_AMB_BOUNDARY;
+        if (g.D2 > Q) continue;
+        if (fabs(g.t1 - tmin) < band || (tmax < INFINITY && fabs(g.t1 - tmax) < band)) *mask |= OR_AMB_TNEAR;
+        if (g.t1 >= tmin && g.t1 < tmax) {
+            out[nh].idx = i;
+            out[nh].seg = seg;
+            out[nh].t = g.t1;
+            out[nh].D2 = g.D2;
+            nh++;
+        }
+    }
+    qsort(out, (size_t)nh, sizeof(or_shit), shit_cmp);
+    return nh;
+}
+
+int or_render_scene(int64_t n, const double* means, const double* quats, const double* scales, const double* opac,
+                    const double* rgb, const or_scene* S, int64_t n_rays, const float* ray_o, const float* ray_d,
+                    const or_params* prm, double* out_rgb, double* out_alpha, double* out_depth,
+                    int32_t* out_nhits, int32_t* out_mask, const double* dl_rgb, const double* dl_alpha,
+                    const double* dl_depth, double* g_means, double* g_quats, double* g_scales, double* g_opac,
+                    double* g_rgb) {
+    double* M = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
+    const size_t cap = (size_t)(n > 0 ? n : 1) + 1;
+    or_shit* seg_hits = (or_shit*)malloc(sizeof(or_shit) * cap);
+    or_shit* comp = (or_shit*)malloc(sizeof(or_shit) * cap * 4);
+    or_shit* sh = (or_shit*)malloc(sizeof(or_shit) * cap);
+    double* alpha = (double*)malloc(sizeof(double) * cap * 4);
+    double* Tb = (double*)malloc(sizeof(double) * cap * 4);
+    if (!M || !seg_hits || !comp || !sh || !alpha || !Tb) {
+        free(M); free(seg_hits); free(comp); free(sh); free(alpha); free(Tb);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) whitening(quats + 4 * i, scales + 3 * i, M + 9 * i);
+    or_job J;
+    memset(&J, 0, sizeof(J));
+    J.n = n; J.means = means; J.quats = quats; J.scales = scales; J.opac = opac; J.rgb = rgb; J.M = M;
+    J.prm = prm;
+    const or_params* P = prm;
+    int rc = 0;
+    for (int64_t r = 0; r < n_rays; ++r) {
+        float so[4][3], sd[4][3], stmin[4];
+        int32_t mask = 0;
+        for (int k = 0; k < 3; ++k) {
+            so[0][k] = ray_o[3 * r + k];
+            sd[0][k] = ray_d[3 * r + k];
+        }
+        stmin[0] = (float)P->t_near;
+        double C[3] = {0, 0, 0}, depth = 0.0, Tr = 1.0, E[3] = {0, 0, 0};
+        int64_t count = 0, nsh = 0;
+        int cut = 0, shadow_used = 0;
+        float sdir[3] = {0, 0, 0}, sP[3] = {0, 0, 0}, sdist = 0.f, alb[3] = {0, 0, 0};
+        for (int seg = 0; seg <= S->max_bounces; ++seg) {
+            float t_tri = INFINITY;
+            const int64_t tri = nearest_tri(S, so[seg], sd[seg], stmin[seg], INFINITY, &t_tri, &mask);
+            const int64_t nh = gather_hits(&J, so[seg], sd[seg], stmin[seg], tri >= 0 ? (double)t_tri : INFINITY, seg,
+                                           seg_hits, &mask);
+            for (int64_t h = 0; h < nh && !cut; ++h) {
+                if (count >= P->k_max) {
+                    cut = 1;
+                    break;
+                }
+                const int64_t i = seg_hits[h].idx;
+                const double al = opac[i] * exp(-0.5 * seg_hits[h].D2);
+                const double w = Tr * al;
+                for (int ch = 0; ch < 3; ++ch) C[ch] += w * rgb[3 * i + ch];
+                if (seg == 0) depth += w * seg_hits[h].t;
+                comp[count] = seg_hits[h];
+                alpha[count] = al;
+                Tb[count] = Tr;
+                Tr *= (1.0 - al);
+                if (h + 1 < nh && fabs(seg_hits[h + 1].t - seg_hits[h].t) < OR_TIE_REL * fmax(1.0, seg_hits[h].t))
+                    mask |= OR_AMB_TIE;
+                if (fabs(Tr - P->eps1) < 1e-4 * P->eps1) mask |= OR_AMB_EPS1;
+                count++;
+                if (Tr < P->eps1) cut = 1;
+            }
+            /* the environment term of this segment */
+            if (tri < 0) {
+                for (int ch = 0; ch < 3; ++ch) E[ch] = P->bg[ch];
+                break;
+            }
+            if (S->mat[tri] == 1) {
+                float dummy[3];
+                reflect_f32(so[seg], sd[seg], t_tri, S->verts + 9 * tri, sP, dummy);
+                shadow_ray_f32(sP, S->light, sdir, &sdist);
+                float t_occ = 0.f;
+                const int64_t occ = nearest_tri(S, sP, sdir, S->eps_off, sdist, &t_occ, &mask);
+                double Ts = 0.0;
+                if (occ < 0) {
+                    nsh = gather_hits(&J, sP, sdir, S->eps_off, sdist, -1, sh, &mask);
+                    Ts = 1.0;
+                    for (int64_t h = 0; h < nsh; ++h) Ts *= 1.0 - opac[sh[h].idx] * exp(-0.5 * sh[h].D2);
+                    shadow_used = 1;
+                }
+                for (int ch = 0; ch < 3; ++ch) {
+                    alb[ch] = S->albedo[3 * tri + ch];
+                    E[ch] = alb[ch] * Ts;
+                }
+                break;
+            }
+            /* mirror */
+            if (cut || seg == S->max_bounces) break;
+            reflect_f32(so[seg], sd[seg], t_tri, S->verts + 9 * tri, so[seg + 1], sd[seg + 1]);
+            stmin[seg + 1] = S->eps_off;
+        }
+        for (int ch = 0; ch < 3; ++ch) out_rgb[3 * r + ch] = C[ch] + Tr * E[ch];
+        out_alpha[r] = 1.0 - Tr;
+        out_depth[r] = depth;
+        out_nhits[r] = (int32_t)count;
+        out_mask[r] = mask;
+        if (!dl_rgb) continue;
+        const double* gc = dl_rgb + 3 * r;
+        const double ga = dl_alpha ? dl_alpha[r] : 0.0;
+        const double gd = dl_depth ? dl_depth[r] : 0.0;
+        /* composited hits, back to front over the segments: U starts at the environment term */
+        double U[3] = {E[0], E[1], E[2]}, UA = 0.0, UD = 0.0;
+        for (int64_t h = count - 1; h >= 0; --h) {
+            const int64_t i = comp[h].idx;
+            const int s = comp[h].seg;
+            const double* c = rgb + 3 * i;
+            const double a = alpha[h], Ti = Tb[h];
+            const double tk = s == 0 ? comp[h].t : 0.0;  /* depth counts the first segment */
+            double dLda = ga * Ti * (1.0 - UA) + gd * Ti * (tk - UD);
+            for (int ch = 0; ch < 3; ++ch) dLda += gc[ch] * Ti * (c[ch] - U[ch]);
+            for (int ch = 0; ch < 3; ++ch) U[ch] = a * c[ch] + (1.0 - a) * U[ch];
+            UA = a + (1.0 - a) * UA;
+            UD = a * tk + (1.0 - a) * UD;
+            double v[14];
+            memset(v, 0, sizeof(v));
+            for (int ch = 0; ch < 3; ++ch) v[11 + ch] = gc[ch] * Ti * a;
+            const double od[3] = {so[s][0], so[s][1], so[s][2]}, dd[3] = {sd[s][0], sd[s][1], sd[s][2]};
+            param_chain(&J, od, dd, i, a, dLda, s == 0 ? gd * Ti * a : 0.0, v);
+            push_contrib(&J, i, v);
+        }
+        /* shadow hits: d(T_final a T_s)/dalpha_j = -T_final a prod_{k != j} (1 - alpha_k) */
+        if (shadow_used && nsh > 0) {
+            const double ga_s = (gc[0] * alb[0] + gc[1] * alb[1] + gc[2] * alb[2]) * Tr;
+            for (int64_t h = 0; h < nsh; ++h) {
+                double others = 1.0;
+                for (int64_t k = 0; k < nsh; ++k)
+                    if (k != h) others *= 1.0 - opac[sh[k].idx] * exp(-0.5 * sh[k].D2);
+                const int64_t i = sh[h].idx;
+                const double a = opac[i] * exp(-0.5 * sh[h].D2);
+                double v[14];
+                memset(v, 0, sizeof(v));
+                const double od[3] = {sP[0], sP[1], sP[2]}, dd[3] = {sdir[0], sdir[1], sdir[2]};
+                param_chain(&J, od, dd, i, a, -ga_s * others, 0.0, v);
+                push_contrib(&J, i, v);
+            }
+        }
+    }
+    if (J.failed) rc = -1;
+    for (int64_t c = 0; c < J.n_contrib; ++c) {
+        const int64_t i = J.contrib[c].idx;
+        const double* v = J.contrib[c].v;
+        for (int k = 0; k < 3; ++k) g_means[3 * i + k] += v[k];
+        for (int k = 0; k < 4; ++k) g_quats[4 * i + k] += v[3 + k];
+        for (int k = 0; k < 3; ++k) g_scales[3 * i + k] += v[7 + k];
+        g_opac[i] += v[10];
+        for (int k = 0; k < 3; ++k) g_rgb[3 * i + k] += v[11 + k];
+    }
+    free(J.contrib);
+    free(M); free(seg_hits); free(comp); free(sh); free(alpha); free(Tb);
+    return rc;
 }

@@ -271,3 +271,54 @@ def pixel_grid(cams: Cameras, cam_subset=None, stride: int = 1, crop=None):
         xs.append(gx.ravel().astype(np.int32))
         ys.append(gy.ravel().astype(np.int32))
     return np.concatenate(cs), np.concatenate(xs), np.concatenate(ys)
+
+
+# ------------------------------------------------------------------------------------------
+# Triangle meshes for the mirror / shadow scenes (geometry only; no rendering arithmetic)
+# ------------------------------------------------------------------------------------------
+def uv_sphere(radius=3.0, slices=200, stacks=126, center=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Triangles (T, 3, 3) float32 of a UV sphere: slices x (stacks - 2) quads as two triangles
+    plus a triangle fan at each pole (200 x 126 gives 50,000 triangles), outward winding."""
+    c = np.asarray(center, np.float64)
+    th = np.linspace(0.0, np.pi, stacks + 1)          # polar angle, stacks bands
+    ph = np.linspace(0.0, 2.0 * np.pi, slices + 1)    # azimuth
+    P = np.stack([np.sin(th)[:, None] * np.cos(ph)[None, :], np.cos(th)[:, None] * np.ones_like(ph)[None, :],
+                  np.sin(th)[:, None] * np.sin(ph)[None, :]], -1) * radius + c
+    tris = []
+    for i in range(stacks):
+        for j in range(slices):
+            a, b, cc, d = P[i, j], P[i, j + 1], P[i + 1, j], P[i + 1, j + 1]
+            if i == 0:
+                tris.append((a, d, cc))
+            elif i == stacks - 1:
+                tris.append((a, b, cc))
+            else:
+                tris.append((a, b, d))
+                tris.append((a, d, cc))
+    return np.asarray(tris, np.float32)
+
+
+def ground_plane(y=-4.0, half=40.0) -> np.ndarray:
+    """Two triangles (2, 3, 3) float32 spanning [-half, half]^2 at height y, facing up."""
+    v = np.array([[-half, y, -half], [half, y, -half], [half, y, half], [-half, y, half]], np.float32)
+    return np.stack([v[[0, 2, 1]], v[[0, 3, 2]]]).astype(np.float32)
+
+
+def mirror_scene_mesh(slices=200, stacks=126, radius=3.0, plane_y=-4.0, plane_half=40.0,
+                      light=(10.0, 15.0, -10.0), albedo=0.8, max_bounces=2, eps_off=1e-3) -> dict:
+    """A mirror UV sphere at the origin and a diffuse grey ground plane lit by one point light."""
+    sph = uv_sphere(radius, slices, stacks)
+    gp = ground_plane(plane_y, plane_half)
+    verts = np.concatenate([sph, gp])
+    mat = np.concatenate([np.zeros(len(sph), np.int32), np.ones(len(gp), np.int32)])
+    alb = np.zeros((len(verts), 3), np.float32)
+    alb[len(sph):] = albedo
+    return {"verts": verts, "mat": mat, "albedo": alb, "light": tuple(float(x) for x in light),
+            "max_bounces": int(max_bounces), "eps_off": float(eps_off)}
+
+
+def workload_mirror(seed: int = 0, n: int = 2_000_000, slices=200, stacks=126):
+    """Secondary rays: 2M Gaussians of the unbounded distribution, a 50,000-triangle mirror
+    sphere (radius 3) and a diffuse ground plane (y = -4, grey 0.8) lit from (10, 15, -10);
+    one 1280 x 832 camera of the ring, up to two mirror bounces and one shadow ray."""
+    return (scene_unbounded(n, seed), mirror_scene_mesh(slices, stacks), ring_cameras().select([0]))
