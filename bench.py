@@ -51,6 +51,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-train", action="store_true", help="skip the full training-step measurement")
+    p.add_argument("--no-mirror", action="store_true", help="skip the mirror / shadow scene measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kbuf", type=int, default=None)
@@ -146,6 +147,49 @@ def make_workload(args):
                                       scenes.look_at_camera((0.0, 2.0, 12.0), (0, 0, 0), 640, 416, 60.0)])
         wl = scenes.Workload(wl.name + "_small2cams", wl.scene, cams, wl.Q, wl.eps1, wl.k_max, wl.background, True)
     return wl
+
+
+def run_mirror(args, dev, timed, stream):
+    """Gaussians with a mirror sphere and a diffuse floor lit through them (rs_render_scene):
+    forward and forward + adjoint rays per second, one 1280 x 832 camera, up to two bounces
+    and one shadow ray per floor hit."""
+    import numpy as np
+    import torch
+    from paper_2501_19196_gb300 import RenderParams, native
+    from paper_2501_19196_gb300.scene import SceneRenderer
+    from workloads import scenes
+    sc, mesh, cams = scenes.workload_mirror()
+    params = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+              for a in (sc.means, sc.quats, sc.scales, sc.opacities, sc.rgb)]
+    P = int(cams.total_rays())
+    prm = RenderParams(Q=scenes.default_Q(), eps1=1e-4, background=(0.0, 0.0, 0.0))
+    sr = SceneRenderer(mesh, tune=native.default_tune(), Q_box=scenes.default_Q(), list_cap=512, shadow_cap=256)
+    outs = (torch.empty((P, 3), device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
+    g_rgb, g_alpha = scenes.upstream_grad(P)
+    d_rgb, d_alpha = torch.from_numpy(g_rgb).to(dev), torch.from_numpy(g_alpha).to(dev)
+    n = params[0].shape[0]
+    grads = {"means": torch.zeros((n, 3), device=dev), "quats": torch.zeros((n, 4), device=dev),
+             "scales": torch.zeros((n, 3), device=dev), "opacities": torch.zeros(n, device=dev),
+             "rgb": torch.zeros((n, 3), device=dev)}
+
+    def step(backward):
+        sr.build(*params)
+        sr.render(cams, prm, out=outs)
+        if backward:
+            for t in grads.values():
+                t.zero_()
+            sr.backward(d_rgb, d_alpha, grads=grads)
+
+    step(True)
+    sr.check_device()
+    ms_f, _ = timed(lambda: step(False), 3, 1)
+    ms_fb, _ = timed(lambda: step(True), 3, 1)
+    sr.check_device()
+    sr.close()
+    return {"workload": "2m_gaussians_mirror_sphere_50k_tris_floor_1280x832", "gaussians": n,
+            "triangles": int(len(mesh["mat"])), "rays": P, "max_bounces": mesh["max_bounces"],
+            "fwd_mrays_s": P / ms_f / 1e3, "fwd_bwd_mrays_s": P / ms_fb / 1e3, "ms_fwd": ms_f, "ms_fwd_bwd": ms_fb,
+            "step": "LBVH rebuild + scene render (mirror bounces, shadow rays) [+ adjoint]"}
 
 
 def oracle_sample_pixels(wl, n_rays, seed=5):
@@ -491,6 +535,11 @@ def run_ours(args):
                  "step": "sigmoid activations + LBVH rebuild + render + L2/D-SSIM loss and gradient + adjoint + "
                          "sigmoid adjoints + Adam (eager launches)"}
 
+    # --- secondary rays: 2M Gaussians, a 50,000-triangle mirror sphere, a lit floor ---
+    mirror = None
+    if not args.no_mirror and args.case == "full":
+        mirror = run_mirror(args, dev, timed, stream)
+
     # --- CPU oracle baseline (rank 0) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -519,7 +568,7 @@ def run_ours(args):
         "plain": plain,
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
         "kernel_ms": kms,
-        "adjoint_without_hit_lists": replay, "training_step": train,
+        "adjoint_without_hit_lists": replay, "training_step": train, "mirror_scene": mirror,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }

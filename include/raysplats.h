@@ -356,6 +356,62 @@ rs_status rs_sigmoid(const float* x, float* y, int64_t count, void* cuda_stream)
 rs_status rs_sigmoid_backward(const float* y, const float* dy, float* dx, int64_t count,
                               void* cuda_stream);
 
+/* ---- Scenes with triangles: mirrors and shadows (Sec. 1, Fig. 1) -------------------------
+ * The paper renders Gaussians together with meshes (mirrors, shadows) but gives no algorithm;
+ * these are the rules implemented (and written out in the oracle):
+ *   - a ray runs in segments; in each, the Gaussians whose entry t1 lies in [t_min, t_tri) are
+ *     composited in (t1, id) order with the eps1 cut and k_max (counted over the whole ray),
+ *     t_tri the nearest triangle (Moller-Trumbore; ties to the lower triangle id);
+ *   - no triangle: the environment term is the background; a diffuse triangle (albedo a):
+ *     a * T_s, T_s the transmittance of a shadow ray from the hit point to the light (product
+ *     of (1 - alpha) over the Gaussians with entry in [eps_off, distance); 0 if a triangle
+ *     blocks it); a mirror triangle: the ray reflects (at most max_bounces times; beyond that
+ *     the term is 0) and the next segment starts at t_min = eps_off;
+ *   - a ray cut by eps1 or k_max keeps the term of the segment it stopped in (a mirror: 0);
+ *   - RGB = composited colour + T_final * term, alpha = 1 - T_final, depth = sum w_i t1_i over
+ *     the first segment; triangle hits, reflections and shadow rays follow fixed FP32
+ *     sequences (the same as the camera rays', round-to-nearest, no contraction);
+ *   - the adjoint is the exact gradient w.r.t. the Gaussian parameters (the mesh and the
+ *     light are fixed).
+ * Only sort_key 0, depth_mode 0 and grad_mode 0 are supported here. */
+typedef struct rs_mesh rs_mesh;
+typedef struct rs_scene_state rs_scene_state;
+
+typedef struct {
+    int64_t n_tri;
+    const float* verts;       /* host float[9 n_tri]: v0, v1, v2 */
+    const int32_t* material;  /* host int32[n_tri]: 0 mirror, 1 diffuse */
+    const float* albedo;      /* host float[3 n_tri] (diffuse) */
+} rs_mesh_desc;
+
+typedef struct {
+    float light[3];           /* point light position */
+    int32_t max_bounces;      /* 0..2 mirror reflections */
+    float eps_off;            /* > 0: t_min of reflected and shadow rays */
+    int32_t list_cap;         /* 1..4096 composited ids kept per ray for the adjoint */
+    int32_t shadow_cap;       /* 1..4096 shadow-ray ids kept per ray */
+} rs_scene_params;
+
+/* Build the mesh's BVH (host, once: median splits, leaves of <= 4 triangles) and upload it. */
+rs_status rs_build_mesh(const rs_mesh_desc* desc, rs_mesh** out);
+rs_status rs_mesh_destroy(rs_mesh* mesh);
+
+/* Render n_cams cameras of the Gaussians `g` (LBVH `accel`) together with `mesh`; outputs as
+ * rs_render.  *inout: the per-ray state the adjoint needs (NULL to create; about
+ * 150 B + 4 B (list_cap + shadow_cap) per ray).  A ray whose ids overflow a list sets a device
+ * error bit that rs_check_device(accel, ...) reports (its gradient is then incomplete). */
+rs_status rs_render_scene(const rs_gaussians* g, const rs_accel* accel, const rs_mesh* mesh,
+                          const rs_scene_params* sp, const rs_camera* cams, int32_t n_cams,
+                          const rs_render_params* params, const rs_tune_params* tune,
+                          rs_frame* out, rs_scene_state** inout, void* cuda_stream);
+
+/* ACCUMULATE the gradient of the last rs_render_scene recorded in `state` w.r.t. the Gaussian
+ * parameters (d_alpha and d_depth may be NULL). */
+rs_status rs_render_scene_backward(const rs_gaussians* g, const rs_accel* accel,
+                                   const rs_scene_state* state, const rs_frame_grad* dl,
+                                   rs_gaussian_grads* out, void* cuda_stream);
+rs_status rs_scene_state_destroy(rs_scene_state* state);
+
 /* Allocation-failure injection, for tests of the out-of-memory paths (the paper has no
  * counterpart).  With n > 0 the n-th device allocation the library makes from now on fails
  * with RS_ERR_OOM (no cudaMalloc is attempted) and the hook disarms itself; n = 0 disarms it.

@@ -562,10 +562,11 @@ rs_status rs_check_device(const rs_accel* accel, const rs_fwd_state* state, void
     if (st) return st;
     const int w = words[0] | words[1];
     if (w) {
-        return set_error(RS_ERR_INTERNAL, "device check failed (bits 0x%x:%s%s%s%s%s)", w,
+        return set_error(RS_ERR_INTERNAL, "device check failed (bits 0x%x:%s%s%s%s%s%s)", w,
                          (w & kErrReplayMismatch) ? " replay-mismatch" : "", (w & kErrBadScene) ? " bad-scene" : "",
                          (w & kErrStack) ? " stack-overflow" : "", (w & kErrLoopGuard) ? " loop-guard" : "",
-                         (w & kErrIndex) ? " index-out-of-range" : "");
+                         (w & kErrIndex) ? " index-out-of-range" : "",
+                         (w & kErrListOverflow) ? " id-list-overflow" : "");
     }
     return RS_OK;
 }

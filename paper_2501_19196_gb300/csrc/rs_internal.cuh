@@ -37,7 +37,8 @@ enum : int {
     kErrBadScene = 2,        // non-finite or non-positive scale / zero quaternion seen in prep
     kErrStack = 4,           // traversal stack overflow (cannot happen for kStackSize >= depth)
     kErrLoopGuard = 8,       // a traversal / round / refit loop exceeded its bound (corrupt tree)
-    kErrIndex = 16           // a node reference or leaf range out of bounds (corrupt tree)
+    kErrIndex = 16,          // a node reference or leaf range out of bounds (corrupt tree)
+    kErrListOverflow = 32    // a per-ray id list of a scene render was too short
 };
 
 struct DevCam {

@@ -43,6 +43,14 @@ class RsGaussianGrads(ctypes.Structure):
     _fields_ = [("d_means", P), ("d_quats", P), ("d_scales", P), ("d_opacities", P), ("d_rgb", P)]
 
 
+class RsMeshDesc(ctypes.Structure):
+    _fields_ = [("n_tri", i64), ("verts", P), ("material", P), ("albedo", P)]
+
+
+class RsSceneParams(ctypes.Structure):
+    _fields_ = [("light", f32 * 3), ("max_bounces", i32), ("eps_off", f32), ("list_cap", i32), ("shadow_cap", i32)]
+
+
 class RsTuneParams(ctypes.Structure):
     _fields_ = [("tile_w", i32), ("tile_h", i32), ("kbuf", i32), ("leaf_size", i32), ("morton_bits", i32),
                 ("persistent", i32), ("block_warps", i32), ("traversal", i32), ("smem_nodes", i32),
@@ -79,6 +87,11 @@ _SIGS = {
     "rs_adam_step": (i32, [P, P, P, P, i64, f32, f32, f32, f32, i32, P]),
     "rs_sigmoid": (i32, [P, P, i64, P]),
     "rs_sigmoid_backward": (i32, [P, P, P, i64, P]),
+    "rs_build_mesh": (i32, [P, P]),
+    "rs_mesh_destroy": (i32, [P]),
+    "rs_render_scene": (i32, [P, P, P, P, P, i32, P, P, P, P, P]),
+    "rs_render_scene_backward": (i32, [P, P, P, P, P, P]),
+    "rs_scene_state_destroy": (i32, [P]),
 }
 
 _LIB = None
