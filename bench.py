@@ -163,7 +163,7 @@ def run_mirror(args, dev, timed, stream):
               for a in (sc.means, sc.quats, sc.scales, sc.opacities, sc.rgb)]
     P = int(cams.total_rays())
     prm = RenderParams(Q=scenes.default_Q(), eps1=1e-4, background=(0.0, 0.0, 0.0))
-    sr = SceneRenderer(mesh, tune=native.default_tune(), Q_box=scenes.default_Q(), list_cap=512, shadow_cap=256)
+    sr = SceneRenderer(mesh, tune=native.default_tune(), Q_box=scenes.default_Q(), list_cap=1024, shadow_cap=1024)
     outs = (torch.empty((P, 3), device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
     g_rgb, g_alpha = scenes.upstream_grad(P)
     d_rgb, d_alpha = torch.from_numpy(g_rgb).to(dev), torch.from_numpy(g_alpha).to(dev)

@@ -365,8 +365,9 @@ rs_status rs_sigmoid_backward(const float* y, const float* dy, float* dx, int64_
  *   - no triangle: the environment term is the background; a diffuse triangle (albedo a):
  *     a * T_s, T_s the transmittance of a shadow ray from the hit point to the light (product
  *     of (1 - alpha) over the Gaussians with entry in [eps_off, distance); 0 if a triangle
- *     blocks it); a mirror triangle: the ray reflects (at most max_bounces times; beyond that
- *     the term is 0) and the next segment starts at t_min = eps_off;
+ *     blocks it or if the product falls below eps1, the shadow ray's own cut); a mirror
+ *     triangle: the ray reflects (at most max_bounces times; beyond that the term is 0) and
+ *     the next segment starts at t_min = eps_off;
  *   - a ray cut by eps1 or k_max keeps the term of the segment it stopped in (a mirror: 0);
  *   - RGB = composited colour + T_final * term, alpha = 1 - T_final, depth = sum w_i t1_i over
  *     the first segment; triangle hits, reflections and shadow rays follow fixed FP32

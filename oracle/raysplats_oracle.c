@@ -834,7 +834,8 @@ double or_chi2_3_quantile(double p) {
 /*     - no triangle: the environment term is the background;                              */
 /*     - diffuse triangle (albedo a): the term is a * T_s, T_s the transmittance of a     */
 /*       shadow ray from the hit point to the light: the product of (1 - alpha) over the   */
-/*       Gaussians it hits (entry in [eps_off, distance)), 0 if a triangle blocks it;      */
+/*       Gaussians it hits (entry in [eps_off, distance)); 0 if a triangle blocks it or    */
+/*       the product falls below eps1 (the shadow ray's own cut, as for camera rays);     */
 /*     - mirror triangle: the ray reflects and continues (at most max_bounces times; past  */
 /*       that the term is 0).                                                              */
 /*   A ray cut by eps1 or k_max takes the term of the segment it stopped in (a mirror      */
@@ -1051,7 +1052,9 @@ int or_render_scene(int64_t n, const double* means, const double* quats, const d
                     nsh = gather_hits(&J, sP, sdir, S->eps_off, sdist, -1, sh, &mask);
                     Ts = 1.0;
                     for (int64_t h = 0; h < nsh; ++h) Ts *= 1.0 - opac[sh[h].idx] * exp(-0.5 * sh[h].D2);
-                    shadow_used = 1;
+                    if (fabs(Ts - P->eps1) < 1e-4 * P->eps1) mask |= OR_AMB_EPS1;
+                    if (Ts < P->eps1) Ts = 0.0;  /* opaque: the shadow ray's eps1 cut */
+                    shadow_used = Ts > 0.0;
                 }
                 for (int ch = 0; ch < 3; ++ch) {
                     alb[ch] = S->albedo[3 * tri + ch];

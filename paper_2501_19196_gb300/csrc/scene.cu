@@ -331,14 +331,16 @@ __device__ bool composite_segment(const SceneArgs& S, const NodeSrc& nodes, int6
     }
 }
 
-// product of (1 - alpha) over the Gaussians with entry in [tmin, tmax) along the ray; ids
-// recorded for the adjoint
+// product of (1 - alpha) over the Gaussians with entry in [tmin, tmax) along the ray, ids
+// recorded for the adjoint; 0 (and no ids) once it falls below eps1: the shadow ray's cut.
+// The product only decreases, so stopping there gives the same answer in any order.
 __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, int64_t pix, const float3 o,
                                       const float3 d, float tmin, float tmax, int& n_out) {
     const TraceParams& P = S.F.P;
     const float4* __restrict__ rec = S.F.rec;
     const float4* __restrict__ sph = S.F.sph;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float eps = fmaxf(P.eps1, 1e-30f);
     float Ts = 1.f;
     int n = 0;
     int st[kStackSize];
@@ -370,6 +372,10 @@ __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, 
                                          __ldg(rec + 4 * q + 2), P.Q, tmin, h);
                     if (!h.hit || !(h.t1 < tmax)) continue;
                     Ts = __fmul_rn(Ts, __fsub_rn(1.f, response_alpha(__ldg(rec + 4 * q + 3).x, h.D2)));
+                    if (Ts < eps) {
+                        n_out = 0;
+                        return 0.f;
+                    }
                     if (n < S.shadow_cap) S.sids[pix * S.shadow_cap + n] = q;
                     else atomicOr(S.F.err, kErrListOverflow);
                     ++n;

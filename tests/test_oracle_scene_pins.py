@@ -108,6 +108,13 @@ def test_shadow_ray_through_one_gaussian_closed_form():
     blocker = _quad(y=7.0, half=1.0, mat=1, albedo=(1.0, 1.0, 1.0))
     out2 = oracle.render_scene(sc, _mesh([(tris, mat, alb), blocker]), o, d, Q99)
     np.testing.assert_array_equal(out2["rgb"][0], 0.0)
+    # the shadow ray's own eps1 cut: a product of (1 - alpha) below eps1 is opaque
+    two = _iso([[0.0, 4.0, 0.0], [0.0, 6.0, 0.0]], 0.1, [0.6, 0.6], [[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    a = float(np.float32(0.6))
+    lit = oracle.render_scene(two, _mesh([(tris, mat, alb)]), o, d, Q99, eps1=0.1)
+    np.testing.assert_allclose(lit["rgb"][0], np.float32([0.5, 0.6, 0.7]) * (1 - a) ** 2, atol=1e-6)
+    cut = oracle.render_scene(two, _mesh([(tris, mat, alb)]), o, d, Q99, eps1=0.2)
+    np.testing.assert_array_equal(cut["rgb"][0], 0.0)
 
 
 @pytest.mark.parametrize("seed", [1, 2])
