@@ -804,8 +804,9 @@ __device__ __forceinline__ void scatter_grad_warp(float4* __restrict__ gtmp, int
 // ---------------------------------------------------------------------------------------------
 // List replay (the paper's index-buffer adjoint, Sec. 3 and Sec. 5): the forward pass wrote
 // the sorted ids of each ray's first list_cap composited hits; a ray with n <= list_cap hits is
-// replayed from that list back to front, with no traversal.  The whole warp calls it
-// (converged); lanes with n = 0 only take part in the scatter.
+// replayed from that list back to front, with no traversal.  Lanes replay different Gaussians
+// at any one step, so each lane issues its own float4 atomics (warp aggregation, which pays
+// in the packet re-traversal where lanes share Gaussians, costs more here than it saves).
 // ---------------------------------------------------------------------------------------------
 template <bool COUNT, bool DEPTH>
 __device__ __forceinline__ void replay_list(const float4* __restrict__ rec, const TraceParams& P, int64_t pix,
@@ -828,7 +829,11 @@ __device__ __forceinline__ void replay_list(const float4* __restrict__ rec, cons
                 k = 0;
             }
         }
-        scatter_grad_warp(gtmp, jout, v);
+        if (jout >= 0) {
+            float4* gp = gtmp + 4 * jout;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) atomicAdd(gp + q, v[q]);
+        }
     }
 }
 
