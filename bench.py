@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-train", action="store_true", help="skip the full training-step measurement")
     p.add_argument("--no-mirror", action="store_true", help="skip the mirror / shadow scene measurement")
+    p.add_argument("--mirror-only", action="store_true", help="only the mirror / shadow scene measurement")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--kbuf", type=int, default=None)
@@ -149,7 +150,24 @@ def make_workload(args):
     return wl
 
 
-def run_mirror(args, dev, timed, stream):
+def _timed_events(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)  # L2 flush (untimed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps, None
+
+
+def run_mirror(args, dev, timed=None, stream=None):
     """Gaussians with a mirror sphere and a diffuse floor lit through them (rs_render_scene):
     forward and forward + adjoint rays per second, one 1280 x 832 camera, up to two bounces
     and one shadow ray per floor hit."""
@@ -180,10 +198,14 @@ def run_mirror(args, dev, timed, stream):
                 t.zero_()
             sr.backward(d_rgb, d_alpha, grads=grads)
 
+    if timed is None:
+        stream = torch.cuda.current_stream()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev)
+        timed = lambda fn, k, w: _timed_events(fn, k, w, flush, stream)  # noqa: E731
     step(True)
     sr.check_device()
-    ms_f, _ = timed(lambda: step(False), 3, 1)
-    ms_fb, _ = timed(lambda: step(True), 3, 1)
+    ms_f, _ = timed(lambda: step(False), max(1, min(3, args.steps)), 1)
+    ms_fb, _ = timed(lambda: step(True), max(1, min(3, args.steps)), 1)
     sr.check_device()
     sr.close()
     return {"workload": "2m_gaussians_mirror_sphere_50k_tris_floor_1280x832", "gaussians": n,
@@ -276,8 +298,14 @@ def run_ours(args):
     from workloads import scenes
 
     native.load()
-    wl = make_workload(args)
     dev = torch.device("cuda", local)
+    if args.mirror_only:
+        m = run_mirror(args, dev)
+        if rank == 0:
+            print(json.dumps({"metric": "Mrays/s of the mirror / shadow scene render", "value": m["fwd_bwd_mrays_s"],
+                              "unit": "Mrays/s", "higher_is_better": True, "mirror_scene": m}), flush=True)
+        return
+    wl = make_workload(args)
     host = [np.ascontiguousarray(a, np.float32) for a in (wl.scene.means, wl.scene.quats, wl.scene.scales,
                                                          wl.scene.opacities, wl.scene.rgb)]
     params = [torch.from_numpy(a).to(dev) for a in host]

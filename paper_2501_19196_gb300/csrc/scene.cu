@@ -2,13 +2,13 @@
 // a point light through the Gaussians (the paper's mesh / mirror / shadow scenes, Sec. 1 and
 // Fig. 1; the paper gives no algorithm, the rules are stated in include/raysplats.h).
 //
-// Per ray (one lane each; the segments of neighbouring rays stay close, but lanes diverge at
-// the surfaces, so the traversals here are per lane):
-//   segment loop: nearest triangle (mesh BVH, closest hit, ties to the lower triangle id),
-//     then the Gaussians with entry in [t_min, t_tri) composited in (t1, id) order with a
-//     register k-buffer (a pass re-starts after its last composited key on overflow); a
-//     mirror reflects the ray, a diffuse triangle sends a shadow ray to the light (any-hit
-//     over the mesh, then the product of (1 - alpha) over the Gaussians it crosses).
+// Per ray (one lane each, one warp per tile of 32 pixels):
+//   segment loop: nearest triangle (mesh BVH per lane, closest hit, ties to the lower triangle
+//     id), then the Gaussians with entry in [t_min, t_tri) composited in (t1, id) order by the
+//     warp-packet best-first traversal of the camera rays (trace.cuh), which continues each
+//     lane's colour, transmittance and count; a mirror reflects the ray, a diffuse triangle
+//     leaves a shadow ray (any-hit over the mesh per lane, then the product of (1 - alpha)
+//     over the Gaussians it crosses, the warp's shadow rays traced as one packet).
 //   Triangle hits, reflections and shadow rays follow fixed FP32 sequences (explicit
 //   round-to-nearest intrinsics, no contraction), the same the oracle writes out.
 // The adjoint replays the composited hits back to front across the segments from a per-ray
@@ -197,145 +197,17 @@ __device__ __forceinline__ void shadow_ray(const float P[3], const float3 L, flo
 }
 
 // ----------------------------------------------------------------------------------------
-// Gaussians along one segment: composite the hits with entry in [tmin, tmax) in (t1, id)
-// order, continuing the ray's transmittance, colour and count; records ids for the adjoint.
-// Returns true when the ray was cut (eps1 or k_max).
+// Shadow rays, one per lane that has one (`want`), traced as a warp packet: the warp walks the
+// union of the boxes its rays cross (depth first, one node fetch for all lanes) and each lane
+// multiplies (1 - alpha) over the Gaussians with entry in [tmin, tmax) on its own ray, ids
+// recorded for the adjoint.  The product only decreases, so the order of the factors cannot
+// change the eps1 decision: a lane whose product falls below eps1 gets 0 (and no ids) and
+// leaves the packet.
 // ----------------------------------------------------------------------------------------
-__device__ bool composite_segment(const SceneArgs& S, const NodeSrc& nodes, int64_t pix, int seg, const float3 o,
-                                  const float3 d, float tmin, float tmax, float& C0, float& C1, float& C2, float& T,
-                                  float& depth, int& count) {
-    const TraceParams& P = S.F.P;
-    const float4* __restrict__ rec = S.F.rec;
-    const float4* __restrict__ sph = S.F.sph;
-    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-    const float eps = fmaxf(P.eps1, 1e-30f);
-    const float INF = __int_as_float(0x7f800000);
-    const int64_t cap0 = tmax < INF ? pack_key(tmax, 0) : kEmptyKey;
-    int64_t lo_key = -1;
-    int64_t last_key = -1;
-    bool cut = false;
-    int passes = 0;
-    int st_node[kStackSize];
-    float st_e[kStackSize];
-    while (true) {
-        if (++passes > P.max_rounds) {
-            atomicOr(S.F.err, kErrLoopGuard);
-            return true;
-        }
-        int64_t keys[kSceneK];
-#pragma unroll
-        for (int s = 0; s < kSceneK; ++s) keys[s] = kEmptyKey;
-        int64_t cap = cap0;
-        const float tlo = lo_key < 0 ? tmin : key_t(lo_key);
-        int sp = 0, node = nodes.root, visits = 0;
-        // depth-first, near child first; every box whose entry lies below the K-th key and the
-        // cap is visited, so the buffer ends with the K nearest hits beyond lo_key
-        while (true) {
-            if (++visits > P.max_visits) {
-                atomicOr(S.F.err, kErrLoopGuard);
-                return true;
-            }
-            float4 n0, n1, n2, n3;
-            fetch_node(nodes, node, n0, n1, n2, n3);
-            float en0, ex0, en1, ex1;
-            slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
-            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-            const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
-            const float e0 = fmaxf(en0, tlo), e1 = fmaxf(en1, tlo);
-            const float tcap = cap == kEmptyKey ? INF : key_t(cap);
-            const float tK = keys[kSceneK - 1] != kEmptyKey ? key_t(keys[kSceneK - 1]) : INF;
-            bool h0 = e0 <= fminf(ex0, fminf(tcap, tK)), h1 = e1 <= fminf(ex1, fminf(tcap, tK));
-#pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const bool hs = side ? h1 : h0;
-                const int rr = side ? r1 : r0;
-                if (hs && rr < 0) {
-                    const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
-                    for (int q = start; q < start + num; ++q) {
-                        if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
-                        Hit h;
-                        ray_ellipsoid<false>(o, d, __ldg(rec + 4 * q + 0), __ldg(rec + 4 * q + 1),
-                                             __ldg(rec + 4 * q + 2), P.Q, tmin, h);
-                        if (!h.hit) continue;
-                        const int64_t key = pack_key(h.t1, q);
-                        if (key > lo_key && key < cap) {
-                            if (key < keys[kSceneK - 1]) {
-                                if (keys[kSceneK - 1] != kEmptyKey) cap = keys[kSceneK - 1];  // evicted
-                                kbuf_insert_asc<kSceneK>(keys, key);
-                            } else {
-                                cap = key;
-                            }
-                        }
-                    }
-                }
-            }
-            const float tK2 = keys[kSceneK - 1] != kEmptyKey ? key_t(keys[kSceneK - 1]) : INF;
-            const float tcap2 = cap == kEmptyKey ? INF : key_t(cap);
-            const bool i0 = h0 && r0 >= 0 && e0 <= fminf(tcap2, tK2), i1 = h1 && r1 >= 0 && e1 <= fminf(tcap2, tK2);
-            int next = -1;
-            if (i0 && i1) {
-                const bool first0 = e0 <= e1;
-                if (sp < kStackSize) {
-                    st_node[sp] = first0 ? r1 : r0;
-                    st_e[sp] = first0 ? e1 : e0;
-                    ++sp;
-                } else {
-                    atomicOr(S.F.err, kErrStack);
-                }
-                next = first0 ? r0 : r1;
-            } else if (i0) {
-                next = r0;
-            } else if (i1) {
-                next = r1;
-            } else {
-                while (sp > 0) {
-                    --sp;
-                    const float tK3 = keys[kSceneK - 1] != kEmptyKey ? key_t(keys[kSceneK - 1]) : INF;
-                    const float tcap3 = cap == kEmptyKey ? INF : key_t(cap);
-                    if (st_e[sp] <= fminf(tcap3, tK3)) {
-                        next = st_node[sp];
-                        break;
-                    }
-                }
-            }
-            if (next < 0) break;
-            node = next;
-        }
-        // composite the pass's hits in order.  Entries are only ever replaced, never removed,
-        // during the traversal: a buffer that is not full holds every hit beyond lo_key.
-        const bool full = keys[kSceneK - 1] != kEmptyKey;
-        while (!cut && keys[0] != kEmptyKey) {
-            const int64_t key = keys[0];
-            const int j = key_j(key);
-            Hit hc;
-            ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
-                                 tmin, hc);
-            const float4 sh = __ldg(rec + 4 * j + 3);
-            const float a = response_alpha(sh.x, hc.D2);
-            const float w = __fmul_rn(T, a);
-            C0 = fmaf(w, sh.y, C0);
-            C1 = fmaf(w, sh.z, C1);
-            C2 = fmaf(w, sh.w, C2);
-            if (seg == 0) depth = fmaf(w, key_t(key), depth);
-            T = __fmul_rn(T, __fsub_rn(1.f, a));
-            if (count < S.list_cap) S.ids[pix * S.list_cap + count] = j | (seg << 30);
-            else atomicOr(S.F.err, kErrListOverflow);
-            ++count;
-            last_key = key;
-            if (T < eps || count >= P.k_max) cut = true;
-            kbuf_pop_front<kSceneK>(keys, kEmptyKey);
-        }
-        if (cut) return true;
-        if (!full) return false;  // every hit of the segment was composited
-        lo_key = last_key;        // the next pass starts after the buffer's last hit
-    }
-}
-
-// product of (1 - alpha) over the Gaussians with entry in [tmin, tmax) along the ray, ids
-// recorded for the adjoint; 0 (and no ids) once it falls below eps1: the shadow ray's cut.
-// The product only decreases, so stopping there gives the same answer in any order.
-__device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, int64_t pix, const float3 o,
-                                      const float3 d, float tmin, float tmax, int& n_out) {
+__device__ float shadow_transmittance_warp(const SceneArgs& S, const NodeSrc& nodes, int64_t pix, bool want,
+                                           const float3 o, const float3 d, float tmin, float tmax, int& n_out) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const TraceParams& P = S.F.P;
     const float4* __restrict__ rec = S.F.rec;
     const float4* __restrict__ sph = S.F.sph;
@@ -343,11 +215,12 @@ __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, 
     const float eps = fmaxf(P.eps1, 1e-30f);
     float Ts = 1.f;
     int n = 0;
-    int st[kStackSize];
+    bool act = want;
+    int st[kStackSize];  // the same on every lane
     int sp = 0, node = nodes.root, visits = 0;
-    while (true) {
+    while (__any_sync(FULL, act)) {
         if (++visits > P.max_visits) {
-            atomicOr(S.F.err, kErrLoopGuard);
+            if (lane == 0) atomicOr(S.F.err, kErrLoopGuard);
             break;
         }
         float4 n0, n1, n2, n3;
@@ -356,25 +229,33 @@ __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, 
         slab2(n0, n1, n2, o, inv, en0, ex0, en1, ex1);
         const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
         const int c0 = __float_as_int(n3.z), c1 = __float_as_int(n3.w);
-        const bool h0 = fmaxf(en0, tmin) <= fminf(ex0, tmax), h1 = fmaxf(en1, tmin) <= fminf(ex1, tmax);
+        const bool h0 = act && fmaxf(en0, tmin) <= fminf(ex0, tmax);
+        const bool h1 = act && fmaxf(en1, tmin) <= fminf(ex1, tmax);
         int next = -1;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const bool hs = side ? h1 : h0;
             const int rr = side ? r1 : r0;
-            if (!hs) continue;
+            if (!__any_sync(FULL, hs)) continue;
             if (rr < 0) {
                 const int start = ~rr, num = leaf_count(nodes, ~rr, side ? c1 : c0);
-                for (int q = start; q < start + num; ++q) {
-                    if (!sphere_may_hit(o, d, __ldg(sph + q))) continue;
+                const uint32_t mask = leaf_sphere_mask(sph, start, num, hs, o, d);
+                uint32_t todo = __reduce_or_sync(FULL, mask);
+                while (todo) {
+                    const int g = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    if (!act || !((mask >> g) & 1u)) continue;
+                    const int q = start + g;
                     Hit h;
-                    ray_ellipsoid<false>(o, d, __ldg(rec + 4 * q + 0), __ldg(rec + 4 * q + 1),
-                                         __ldg(rec + 4 * q + 2), P.Q, tmin, h);
+                    ray_ellipsoid<false>(o, d, __ldg(rec + 4 * q + 0), __ldg(rec + 4 * q + 1), __ldg(rec + 4 * q + 2),
+                                         P.Q, tmin, h);
                     if (!h.hit || !(h.t1 < tmax)) continue;
                     Ts = __fmul_rn(Ts, __fsub_rn(1.f, response_alpha(__ldg(rec + 4 * q + 3).x, h.D2)));
                     if (Ts < eps) {
-                        n_out = 0;
-                        return 0.f;
+                        act = false;
+                        Ts = 0.f;
+                        n = 0;
+                        continue;
                     }
                     if (n < S.shadow_cap) S.sids[pix * S.shadow_cap + n] = q;
                     else atomicOr(S.F.err, kErrListOverflow);
@@ -384,7 +265,7 @@ __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, 
                 next = rr;
             } else if (sp < kStackSize) {
                 st[sp++] = rr;
-            } else {
+            } else if (lane == 0) {
                 atomicOr(S.F.err, kErrStack);
             }
         }
@@ -398,66 +279,77 @@ __device__ float shadow_transmittance(const SceneArgs& S, const NodeSrc& nodes, 
     return Ts;
 }
 
-__global__ void __launch_bounds__(128) k_render_scene(SceneArgs S) {
+// One warp per tile of 32 pixels.  Segment by segment (the segment index is the same on every
+// lane): each lane that still has a segment finds its nearest triangle, then the warp
+// composites the Gaussians before the triangles as one best-first packet, continuing each
+// ray's colour, transmittance and count; a mirror reflects the lane's ray into the next
+// segment, a diffuse triangle leaves a shadow ray, traced by the whole warp at the end.
+__global__ void __launch_bounds__(128, 3) k_render_scene(SceneArgs S) {
     extern __shared__ float4 s_top[];
     const FwdArgs& A = S.F;
     for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
     const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top, A.P.n_gauss, A.err};
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (tile >= A.total_tiles) return;
+    if (tile >= A.total_tiles) return;  // the whole warp
     DevCam cam;
     int px, py;
     int64_t pix;
-    if (!tile_pixel(A, tile, lane, cam, px, py, pix)) return;
+    const bool valid = tile_pixel(A, tile, lane, cam, px, py, pix);
     float3 o3, d3;
     camera_ray(cam, px, py, o3, d3);
+    const float INF = __int_as_float(0x7f800000);
+    const float eps = fmaxf(A.P.eps1, 1e-30f);
     float o[3] = {o3.x, o3.y, o3.z}, d[3] = {d3.x, d3.y, d3.z};
     float tmin = A.P.t_near;
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f, depth = 0.f;
     int count = 0, nsh = -1;
     float E[3] = {0.f, 0.f, 0.f};
-    for (int seg = 0; seg <= S.max_bounces; ++seg) {
-        S.seg[(pix * 3 + seg) * 2] = make_float4(o[0], o[1], o[2], tmin);
-        S.seg[(pix * 3 + seg) * 2 + 1] = make_float4(d[0], d[1], d[2], 0.f);
-        float t_tri;
-        int id, mat;
-        const int tri = mesh_trace<false>(S.mesh, o, d, tmin, __int_as_float(0x7f800000), t_tri, id, mat, A.err);
-        const bool cut = composite_segment(S, ns, pix, seg, make_float3(o[0], o[1], o[2]), make_float3(d[0], d[1], d[2]),
-                                           tmin, tri >= 0 ? t_tri : __int_as_float(0x7f800000), C0, C1, C2, T, depth,
-                                           count);
+    bool alive = valid;  // the lane has a segment to trace
+    bool lit = false;    // the lane ended on a diffuse triangle: its shadow ray is pending
+    float Pp[3] = {0.f, 0.f, 0.f}, dir[3] = {0.f, 0.f, 1.f}, dist = 0.f;
+    float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
+    Counters cnt;
+    int64_t last_key;
+    for (int seg = 0; seg <= S.max_bounces && __any_sync(FULL, alive); ++seg) {
+        float t_tri = INF;
+        int tri = -1, id = 0, mat = 0;
+        if (alive) {
+            S.seg[(pix * 3 + seg) * 2] = make_float4(o[0], o[1], o[2], tmin);
+            S.seg[(pix * 3 + seg) * 2 + 1] = make_float4(d[0], d[1], d[2], 0.f);
+            tri = mesh_trace<false>(S.mesh, o, d, tmin, INF, t_tri, id, mat, A.err);
+        }
+        const SegRange R{tmin, (alive && tri >= 0) ? pack_key(t_tri, 0) : kEmptyKey, (int)((unsigned)seg << 30),
+                         seg == 0};
+        trace_forward_bf<kSceneK, false, 2, false, true>(A.rec, A.sph, ns, A.P, pix, alive, make_float3(o[0], o[1], o[2]),
+                                                         make_float3(d[0], d[1], d[2]), C0, C1, C2, T, depth, last_key,
+                                                         count, cnt, A.err, R);
+        if (!alive) continue;
+        const bool cut = T < eps || count >= A.P.k_max;
         if (tri < 0) {
             E[0] = A.P.bg[0];
             E[1] = A.P.bg[1];
             E[2] = A.P.bg[2];
-            break;
+            alive = false;
+            continue;
         }
         float v0[3], v1[3], v2[3];
         int id2, mat2;
         load_tri(S.mesh, tri, v0, v1, v2, id2, mat2);
         if (mat == 1) {
-            float Pp[3], dir[3], dist;
             hit_point(o, d, t_tri, Pp);
             shadow_ray(Pp, S.light, dir, dist);
-            float t_occ;
-            int oid, omat;
-            const int occ = mesh_trace<true>(S.mesh, Pp, dir, S.eps_off, dist, t_occ, oid, omat, A.err);
-            float Ts = 0.f;
-            nsh = 0;
-            if (occ < 0)
-                Ts = shadow_transmittance(S, ns, pix, make_float3(Pp[0], Pp[1], Pp[2]), make_float3(dir[0], dir[1], dir[2]),
-                                          S.eps_off, dist, nsh);
-            const float4 al = __ldg(S.mesh.albedo + id);
-            E[0] = __fmul_rn(al.x, Ts);
-            E[1] = __fmul_rn(al.y, Ts);
-            E[2] = __fmul_rn(al.z, Ts);
-            S.shadow[pix * 3] = make_float4(Pp[0], Pp[1], Pp[2], dist);
-            S.shadow[pix * 3 + 1] = make_float4(dir[0], dir[1], dir[2], Ts);
-            S.shadow[pix * 3 + 2] = al;
-            break;
+            al = __ldg(S.mesh.albedo + id);
+            lit = true;
+            alive = false;
+            continue;
         }
-        if (cut || seg == S.max_bounces) break;  // mirror: nothing beyond the last bounce
+        if (cut || seg == S.max_bounces) {  // mirror: nothing beyond the last bounce
+            alive = false;
+            continue;
+        }
         float Pn[3], dn[3];
         reflect_ray(o, d, t_tri, v0, v1, v2, Pn, dn);
         for (int k = 0; k < 3; ++k) {
@@ -465,6 +357,28 @@ __global__ void __launch_bounds__(128) k_render_scene(SceneArgs S) {
             d[k] = dn[k];
         }
         tmin = S.eps_off;
+    }
+    // shadow rays: the mesh blocks per lane (any hit), the Gaussians as one warp packet
+    bool want = false;
+    if (lit) {
+        float t_occ;
+        int oid, omat;
+        want = mesh_trace<true>(S.mesh, Pp, dir, S.eps_off, dist, t_occ, oid, omat, A.err) < 0;
+        nsh = 0;
+    }
+    int nw = 0;
+    const float Tw = shadow_transmittance_warp(S, ns, pix, want, make_float3(Pp[0], Pp[1], Pp[2]),
+                                               make_float3(dir[0], dir[1], dir[2]), S.eps_off, dist, nw);
+    if (!valid) return;
+    if (lit) {
+        const float Ts = want ? Tw : 0.f;
+        if (want) nsh = nw;
+        E[0] = __fmul_rn(al.x, Ts);
+        E[1] = __fmul_rn(al.y, Ts);
+        E[2] = __fmul_rn(al.z, Ts);
+        S.shadow[pix * 3] = make_float4(Pp[0], Pp[1], Pp[2], dist);
+        S.shadow[pix * 3 + 1] = make_float4(dir[0], dir[1], dir[2], Ts);
+        S.shadow[pix * 3 + 2] = al;
     }
     A.rgb[3 * pix + 0] = fmaf(T, E[0], C0);
     A.rgb[3 * pix + 1] = fmaf(T, E[1], C1);
@@ -828,6 +742,8 @@ rs_status rs_render_scene(const rs_gaussians* g, const rs_accel* accel, const rs
     SA.shadow = S->shadow;
     SA.ids = S->ids;
     SA.sids = S->sids;
+    P.ids = S->ids;  // the segments' composited ids (segment << 30 | id)
+    P.list_cap = sp->list_cap;
     const int block = 128;
     const int grid = (int)((tiles + 3) / 4);
     const size_t smem = (size_t)accel->n_top * 4 * sizeof(float4);

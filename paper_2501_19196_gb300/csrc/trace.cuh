@@ -1352,20 +1352,37 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
 // hits in order without compositing them, accumulating the colour S and transmittance T2 seen
 // behind its last composited hit until T2 < eps2; (S + T2 background, 1 - T2) is stored per
 // pixel for the adjoint.
-template <int K, bool COUNT, int W, bool EPS2 = false>
+// One segment of a ray that continues a composite already under way (the scene renderer's
+// segments between surfaces): hits with entry in [t0, end) where cap0 = pack_key(end, 0)
+// (kEmptyKey: no end), ids recorded as id | tag, depth accumulated only when `depth` is set.
+struct SegRange {
+    float t0;
+    int64_t cap0;
+    int tag;
+    bool depth;
+};
+
+// SEG = false: a camera ray from scratch (T = 1, nothing composited, entries from t_near).
+// SEG = true: the segment `seg` continues (C, T, depth, count); overflowing ids are reported.
+template <int K, bool COUNT, int W, bool EPS2 = false, bool SEG = false>
 __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                  const TraceParams& P, int64_t pix, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
-                                                 int64_t& last_key, int& count, Counters& cnt, int* err) {
+                                                 int64_t& last_key, int& count, Counters& cnt, int* err,
+                                                 const SegRange seg = SegRange{0.f, kEmptyKey, 0, true}) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float eps = fmaxf(P.eps1, 1e-30f);
     const float INF = __int_as_float(0x7f800000);
-    T = 1.f;
-    C0 = C1 = C2 = 0.f;
-    depth = 0.f;
-    count = 0;
+    const float tmin = SEG ? seg.t0 : P.t_near;
+    const int64_t cap0 = SEG ? seg.cap0 : kEmptyKey;
+    if (!SEG) {
+        T = 1.f;
+        C0 = C1 = C2 = 0.f;
+        depth = 0.f;
+        count = 0;
+    }
     last_key = -1;
     int64_t lo_key = -1;
     int64_t lp_key = -1;  // last key composited or (phase 2) collected
@@ -1386,14 +1403,14 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             keys[s] = kEmptyKey;
         }
         int nk = 0;  // pending keys (slots [0, nk))
-        int64_t cap = kEmptyKey;
-        const float tlo = lo_key < 0 ? P.t_near : key_t(lo_key);
+        int64_t cap = cap0;
+        const float tlo = lo_key < 0 ? tmin : key_t(lo_key);
         auto composite_front = [&]() {
             const int64_t key = keys[0];
             const int j = key_j(key);
             Hit hc;  // the same solve as at insertion time: the same bits
             ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
-                                 P.t_near, hc);
+                                 tmin, hc);
             const float4 sh = __ldg(rec + 4 * j + 3);
             const float a = response_alpha(sh.x, hc.D2);
             if (EPS2 && ph2) {  // phase 2: collect, do not composite
@@ -1411,9 +1428,10 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             C0 = fmaf(w, sh.y, C0);
             C1 = fmaf(w, sh.z, C1);
             C2 = fmaf(w, sh.w, C2);
-            depth = fmaf(w, key_t(key), depth);
+            if (!SEG || seg.depth) depth = fmaf(w, key_t(key), depth);
             T = __fmul_rn(T, __fsub_rn(1.f, a));
-            if (count < P.list_cap) P.ids[pix * P.list_cap + count] = j;  // for the adjoint's list replay
+            if (count < P.list_cap) P.ids[pix * P.list_cap + count] = SEG ? (j | seg.tag) : j;  // for the adjoint
+            else if (SEG) atomicOr(err, kErrListOverflow);
             ++count;
             last_key = key;
             lp_key = key;
@@ -1508,7 +1526,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                 const float4 g1 = __ldg(rec + 4 * qq + 1);
                                 const float4 g2 = __ldg(rec + 4 * qq + 2);
                                 Hit hh;
-                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
+                                ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, tmin, hh);
                                 if (COUNT) cnt.tests++;
                                 if (hh.hit) {
                                     const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
@@ -1559,7 +1577,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             if (!popped || !__any_sync(FULL, active)) break;
         }
         if (active && !done) {
-            if (cap == kEmptyKey) done = true;
+            if (cap == cap0) done = true;  // nothing was dropped: every hit before the end is in
             else lo_key = EPS2 ? lp_key : last_key;
         }
     }
