@@ -1257,19 +1257,22 @@ __device__ __forceinline__ void wq_init(WarpQueue& q) {
 template <bool MAXQ>
 __device__ __forceinline__ bool wq_push(WarpQueue& q, float pr, int node, int lane) {
     const uint32_t bits = wq_bits<MAXQ>(pr);
+    int free_slot = -1;  // this lane's first empty slot
 #pragma unroll
-    for (int s = 0; s < kQSlots; ++s) {
-        const unsigned m = __ballot_sync(0xffffffffu, q.key[s] == wq_empty<MAXQ>());
-        if (m) {
-            const int owner = __ffs(m) - 1;
-            if (lane == owner) {
+    for (int s = kQSlots - 1; s >= 0; --s)
+        if (q.key[s] == wq_empty<MAXQ>()) free_slot = s;
+    const unsigned m = __ballot_sync(0xffffffffu, free_slot >= 0);
+    if (!m) return false;
+    const int owner = __ffs(m) - 1;
+    if (lane == owner) {
+#pragma unroll
+        for (int s = 0; s < kQSlots; ++s)
+            if (free_slot == s) {
                 q.key[s] = bits | (uint32_t)(owner * kQSlots + s);
                 q.nd[s] = node;
             }
-            return true;
-        }
     }
-    return false;
+    return true;
 }
 
 template <bool MAXQ>
@@ -1288,10 +1291,10 @@ __device__ __forceinline__ float wq_top(const WarpQueue& q) {
     return __uint_as_float(v & ~0x7fu);
 }
 
-// pop the extreme entry; returns false when empty
+// pop the extreme entry, whose key v = wq_extreme_key(q) the caller already holds; returns
+// false when empty
 template <bool MAXQ>
-__device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int lane) {
-    const uint32_t v = wq_extreme_key<MAXQ>(q);
+__device__ __forceinline__ bool wq_pop_known(WarpQueue& q, uint32_t v, float& pr, int& node, int lane) {
     if (v == wq_empty<MAXQ>()) return false;
     const int gid = (int)(v & 0x7fu);
     const int owner = gid / kQSlots, slot = gid % kQSlots;
@@ -1307,6 +1310,19 @@ __device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int l
             if (slot == s) q.key[s] = wq_empty<MAXQ>();
     }
     return true;
+}
+
+// pop the extreme entry; returns false when empty
+template <bool MAXQ>
+__device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int lane) {
+    return wq_pop_known<MAXQ>(q, wq_extreme_key<MAXQ>(q), pr, node, lane);
+}
+
+// the priority of extreme key v: +inf (min-queue) / -inf (max-queue) for an empty queue
+template <bool MAXQ>
+__device__ __forceinline__ float wq_key_priority(uint32_t v) {
+    if (v == wq_empty<MAXQ>()) return MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    return __uint_as_float(v & ~0x7fu);
 }
 
 // push with eviction: when the queue is full, the worst entry among the queue and the new one
@@ -1456,11 +1472,12 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         WarpQueue q;
         wq_init<false>(q);
         wq_push<false>(q, -INF, nodes.root, lane);
+        uint32_t qtop = wq_extreme_key<false>(q);  // the queue's minimum key, kept across steps
         int visits = 0;
         while (true) {
             float e_node;
             int node;
-            const bool popped = wq_pop<false>(q, e_node, node, lane);
+            const bool popped = wq_pop_known<false>(q, qtop, e_node, node, lane);
             // a lane needs the node unless its (conservative) entry lies past its bounds
             bool need = false;
             if (popped && active) {
@@ -1571,7 +1588,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     }
                 }
             }
-            const float bound = wq_top<false>(q);  // +inf when empty: composite everything pending
+            qtop = wq_extreme_key<false>(q);
+            const float bound = wq_key_priority<false>(qtop);  // +inf when empty: composite all pending
             while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
             active = active && !done;
             if (!popped || !__any_sync(FULL, active)) break;
