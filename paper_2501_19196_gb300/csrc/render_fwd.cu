@@ -6,15 +6,26 @@
 
 namespace rs {
 
-template <int K, bool PERSIST, bool COUNT, int MODE, bool EPS2 = false>
-__global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
+// The best-first forward (traversal 2, and the eps2 estimator) with K = 32 keeps its pending hits
+// in shared memory (SmemKbuf) instead of registers: 85 registers instead of 128, so 6 CTAs of 4
+// warps per SM instead of 4.  It does not stage top nodes (the rings take that shared memory).
+constexpr bool kFwdSmemKbuf = true;
+
+// dynamic shared memory of a forward launch: staged top nodes, or the warps' k-buffer rings
+template <int K>
+static size_t ring_smem_bytes(int block) { return (size_t)(block / 32) * K * 32 * sizeof(int64_t); }
+
+template <int K, bool PERSIST, bool COUNT, int MODE, bool EPS2 = false, bool SMEMK = false>
+__global__ void __launch_bounds__(128, SMEMK ? 6 : 4) k_render_fwd(FwdArgs A) {
     extern __shared__ float4 s_top[];
-    if (MODE != 3)
+    if (MODE != 3 && !SMEMK)
         for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
     __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
+    const NodeSrc ns{A.nodes, s_top, (MODE != 3 && !SMEMK && A.n_top > 0) ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top,
                      A.P.n_gauss, A.err};
     const int lane = threadIdx.x & 31;
+    int64_t* kb_col = nullptr;  // this lane's column of its warp's ring block
+    if (SMEMK) kb_col = reinterpret_cast<int64_t*>(s_top) + (threadIdx.x >> 5) * (K * 32) + lane;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
     uint32_t rays = 0;
@@ -37,6 +48,10 @@ __global__ void __launch_bounds__(128, 4) k_render_fwd(FwdArgs A) {
         if (MODE == 3)
             trace_forward_bf<K, COUNT, 4>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
+        else if (MODE == 2 && SMEMK)
+            trace_forward_bf<K, COUNT, 2, EPS2, false, true>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth,
+                                                             last_key, count, cnt, A.err,
+                                                             SegRange{0.f, kEmptyKey, 0, true}, kb_col);
         else if (MODE == 2)
             trace_forward_bf<K, COUNT, 2, EPS2>(A.rec, A.sph, ns, A.P, pix, valid, o, d, C0, C1, C2, T, depth, last_key, count,
                                           cnt, A.err);
@@ -119,6 +134,14 @@ static int occupancy_fwd(int block, size_t smem) {
 template <int K, bool COUNT>
 static int occupancy_fwd_m(int block, int mode, size_t smem) {
     if (mode == 3) return occupancy_fwd<K, COUNT, 3>(block, 0);
+    if constexpr (kFwdSmemKbuf && K == 32) {
+        if (mode == 2) {  // the eps2 estimator's kernel has the same footprint
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_fwd<K, true, COUNT, 2, false, true>, block,
+                                                          ring_smem_bytes<K>(block));
+            return nb;
+        }
+    }
     if (mode == 2) return occupancy_fwd<K, COUNT, 2>(block, smem);
     if (mode == 1) return occupancy_fwd<K, COUNT, 1>(block, smem);
     return occupancy_fwd<K, COUNT, 0>(block, smem);
@@ -138,6 +161,16 @@ static void launch_fwd_mode(const FwdArgs& A, int mode, int grid, int block, cud
     const size_t sm = smem_bytes(A.n_top);
     // the eps2 estimator's phase 2 is built into the best-first traversal only (every traversal
     // order gives the same result, so the order is a free choice)
+    if constexpr (kFwdSmemKbuf && K == 32) {
+        if (A.P.grad_mode == 1) {
+            k_render_fwd<K, PERSIST, COUNT, 2, true, true><<<grid, block, ring_smem_bytes<K>(block), st>>>(A);
+            return;
+        }
+        if (mode == 2) {
+            k_render_fwd<K, PERSIST, COUNT, 2, false, true><<<grid, block, ring_smem_bytes<K>(block), st>>>(A);
+            return;
+        }
+    }
     if (A.P.grad_mode == 1) k_render_fwd<K, PERSIST, COUNT, 2, true><<<grid, block, sm, st>>>(A);
     else if (mode == 3) k_render_fwd<K, PERSIST, COUNT, 3><<<grid, block, 0, st>>>(A);
     else if (mode == 2) k_render_fwd<K, PERSIST, COUNT, 2><<<grid, block, sm, st>>>(A);

@@ -283,15 +283,16 @@ __device__ float shadow_transmittance_warp(const SceneArgs& S, const NodeSrc& no
 // lane): each lane that still has a segment finds its nearest triangle, then the warp
 // composites the Gaussians before the triangles as one best-first packet, continuing each
 // ray's colour, transmittance and count; a mirror reflects the lane's ray into the next
-// segment, a diffuse triangle leaves a shadow ray, traced by the whole warp at the end.
-__global__ void __launch_bounds__(128, 3) k_render_scene(SceneArgs S) {
-    extern __shared__ float4 s_top[];
+// segment, a diffuse triangle leaves a shadow ray, traced by the whole warp at the end.  The
+// segments' pending hits sit in shared-memory rings (SmemKbuf, one K-slot block per warp), so
+// top nodes are not staged.
+__global__ void __launch_bounds__(128, 4) k_render_scene(SceneArgs S) {
+    extern __shared__ float4 s_top[];  // the warps' k-buffer rings
     const FwdArgs& A = S.F;
-    for (int i = threadIdx.x; i < 4 * A.n_top; i += blockDim.x) s_top[i] = A.top[i];
-    __syncthreads();
-    const NodeSrc ns{A.nodes, s_top, A.n_top > 0 ? kTopRef : 0, A.wide, A.P.n_nodes, A.n_top, A.P.n_gauss, A.err};
+    const NodeSrc ns{A.nodes, s_top, 0, A.wide, A.P.n_nodes, A.n_top, A.P.n_gauss, A.err};
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    int64_t* kb_col = reinterpret_cast<int64_t*>(s_top) + (threadIdx.x >> 5) * (kSceneK * 32) + lane;
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (tile >= A.total_tiles) return;  // the whole warp
     DevCam cam;
@@ -323,9 +324,9 @@ __global__ void __launch_bounds__(128, 3) k_render_scene(SceneArgs S) {
         }
         const SegRange R{tmin, (alive && tri >= 0) ? pack_key(t_tri, 0) : kEmptyKey, (int)((unsigned)seg << 30),
                          seg == 0};
-        trace_forward_bf<kSceneK, false, 2, false, true>(A.rec, A.sph, ns, A.P, pix, alive, make_float3(o[0], o[1], o[2]),
-                                                         make_float3(d[0], d[1], d[2]), C0, C1, C2, T, depth, last_key,
-                                                         count, cnt, A.err, R);
+        trace_forward_bf<kSceneK, false, 2, false, true, true>(A.rec, A.sph, ns, A.P, pix, alive,
+                                                               make_float3(o[0], o[1], o[2]), make_float3(d[0], d[1], d[2]),
+                                                               C0, C1, C2, T, depth, last_key, count, cnt, A.err, R, kb_col);
         if (!alive) continue;
         const bool cut = T < eps || count >= A.P.k_max;
         if (tri < 0) {
@@ -746,7 +747,7 @@ rs_status rs_render_scene(const rs_gaussians* g, const rs_accel* accel, const rs
     P.list_cap = sp->list_cap;
     const int block = 128;
     const int grid = (int)((tiles + 3) / 4);
-    const size_t smem = (size_t)accel->n_top * 4 * sizeof(float4);
+    const size_t smem = (size_t)(block / 32) * kSceneK * 32 * sizeof(int64_t);
     k_render_scene<<<std::max(grid, 1), block, smem, s>>>(SA);
     st = cuda_check("scene render launch");
     if (st) return st;

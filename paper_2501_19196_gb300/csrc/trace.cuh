@@ -26,7 +26,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "rs_internal.cuh"
+
 #include "rs_render.h"
 
 namespace rs {
@@ -1283,14 +1286,6 @@ __device__ __forceinline__ uint32_t wq_extreme_key(const WarpQueue& q) {
     return MAXQ ? __reduce_max_sync(0xffffffffu, v) : __reduce_min_sync(0xffffffffu, v);
 }
 
-// extreme priority over the whole queue (uniform); +inf (min-queue) / -inf (max-queue) if empty
-template <bool MAXQ>
-__device__ __forceinline__ float wq_top(const WarpQueue& q) {
-    const uint32_t v = wq_extreme_key<MAXQ>(q);
-    if (v == wq_empty<MAXQ>()) return MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
-    return __uint_as_float(v & ~0x7fu);
-}
-
 // pop the extreme entry, whose key v = wq_extreme_key(q) the caller already holds; returns
 // false when empty
 template <bool MAXQ>
@@ -1312,12 +1307,6 @@ __device__ __forceinline__ bool wq_pop_known(WarpQueue& q, uint32_t v, float& pr
     return true;
 }
 
-// pop the extreme entry; returns false when empty
-template <bool MAXQ>
-__device__ __forceinline__ bool wq_pop(WarpQueue& q, float& pr, int& node, int lane) {
-    return wq_pop_known<MAXQ>(q, wq_extreme_key<MAXQ>(q), pr, node, lane);
-}
-
 // the priority of extreme key v: +inf (min-queue) / -inf (max-queue) for an empty queue
 template <bool MAXQ>
 __device__ __forceinline__ float wq_key_priority(uint32_t v) {
@@ -1325,11 +1314,12 @@ __device__ __forceinline__ float wq_key_priority(uint32_t v) {
     return __uint_as_float(v & ~0x7fu);
 }
 
-// push with eviction: when the queue is full, the worst entry among the queue and the new one
-// (largest priority for the min-queue, smallest for the max-queue) is dropped; returns true and
-// its (rounded, conservative) priority in *evicted when something was dropped.
+// push with displacement: when the queue is full, the worst entry among the queue and the new
+// one (largest priority for the min-queue, smallest for the max-queue) does not stay; returns
+// true with its (rounded, conservative) priority and node in out_pr / out_node.
 template <bool MAXQ>
-__device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, int lane, float& evicted) {
+__device__ __forceinline__ bool wq_push_displace(WarpQueue& q, float pr, int node, int lane, float& out_pr,
+                                                 int& out_node) {
     if (wq_push<MAXQ>(q, pr, node, lane)) return false;
     uint32_t v = q.key[0];
 #pragma unroll
@@ -1339,11 +1329,17 @@ __device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, 
     const uint32_t wb = v & ~0x7fu;
     const bool replace = MAXQ ? (wb < nb) : (wb > nb);
     if (!replace) {
-        evicted = __uint_as_float(nb);
+        out_pr = __uint_as_float(nb);
+        out_node = node;
         return true;
     }
     const int gid = (int)(v & 0x7fu);
     const int owner = gid / kQSlots, slot = gid % kQSlots;
+    int mine = q.nd[0];
+#pragma unroll
+    for (int s = 1; s < kQSlots; ++s)
+        if (slot == s) mine = q.nd[s];
+    out_node = __shfl_sync(0xffffffffu, mine, owner);
     if (lane == owner) {
 #pragma unroll
         for (int s = 0; s < kQSlots; ++s)
@@ -1352,8 +1348,47 @@ __device__ __forceinline__ bool wq_push_evict(WarpQueue& q, float pr, int node, 
                 q.nd[s] = node;
             }
     }
-    evicted = __uint_as_float(wb);
+    out_pr = __uint_as_float(wb);
     return true;
+}
+
+// Nodes displaced from a full queue, kept for later in the same pass.  Dropping such a node
+// instead caps the pass at its priority, and when no hit lies between the pass's start and
+// that priority the pass composites nothing and the next one repeats it exactly: a live lock
+// on rays that start among many overlapping boxes (reflected rays inside the cloud).  The list
+// is warp-uniform (every lane holds the same entries); only a full list drops a node.
+// The list's entries live in local memory (touched only when the queue is full); its fill n and
+// its best priority (smallest for the min-queue, largest for the max-queue, +-inf when empty)
+// are kept by the caller in registers.
+constexpr int kDeferSlots = 64;
+struct WarpDefer {
+    int node[kDeferSlots];
+    float pr[kDeferSlots];
+};
+
+template <bool MAXQ>
+__device__ __forceinline__ float wd_none() {
+    return MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+}
+
+// keep a displaced node; false when the list is full (the caller drops the node then)
+template <bool MAXQ>
+__device__ __forceinline__ bool wd_add(WarpDefer& w, int& n, float& best, float pr, int node) {
+    if (n >= kDeferSlots) return false;
+    w.node[n] = node;
+    w.pr[n] = pr;
+    ++n;
+    best = MAXQ ? fmaxf(best, pr) : fminf(best, pr);
+    return true;
+}
+
+// move kept nodes back into the (empty) queue, as many as fit; returns the queue's extreme key
+template <bool MAXQ>
+__device__ __forceinline__ uint32_t wd_refill(const WarpDefer& w, int& n, float& best, WarpQueue& q, int lane) {
+    while (n > 0 && wq_push<MAXQ>(q, w.pr[n - 1], w.node[n - 1], lane)) --n;
+    best = wd_none<MAXQ>();
+    for (int i = 0; i < n; ++i) best = MAXQ ? fmaxf(best, w.pr[i]) : fminf(best, w.pr[i]);
+    return wq_extreme_key<MAXQ>(q);
 }
 
 // warp-wide min / max of non-negative floats (their bit patterns order as unsigned integers)
@@ -1368,6 +1403,88 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
 // hits in order without compositing them, accumulating the colour S and transmittance T2 seen
 // behind its last composited hit until T2 < eps2; (S + T2 background, 1 - T2) is stored per
 // pixel for the adjoint.
+// The pending-hit buffer of the best-first forward, two layouts with one interface.  Keys are
+// kept ascending; front() is the nearest pending key (kEmptyKey when none) and last() the K-th
+// (kEmptyKey unless the buffer is full).
+//
+// RegKbuf: K 64-bit keys in registers, compare-exchange networks sized by the warp's fill.
+template <int K>
+struct RegKbuf {
+    int64_t keys[K];
+    int nk;  // occupied slots [0, nk)
+    __device__ __forceinline__ explicit RegKbuf(int64_t*) {}
+    __device__ __forceinline__ void reset() {
+#pragma unroll
+        for (int s = 0; s < K; ++s) keys[s] = kEmptyKey;
+        nk = 0;
+    }
+    __device__ __forceinline__ int64_t front() const { return keys[0]; }
+    __device__ __forceinline__ int64_t last() const { return keys[K - 1]; }
+    // insert `key` (< last()) where `ins`; all 32 lanes call, converged
+    __device__ __forceinline__ void insert_warp(bool ins, int64_t key) { kbuf_insert_warp<K>(keys, nk, ins, key); }
+    // drop front() in the calling lanes (converged among themselves)
+    __device__ __forceinline__ void pop(unsigned group) { kbuf_pop_warp<K>(keys, nk, kEmptyKey, group); }
+    // drop every key >= cap
+    __device__ __forceinline__ void drop_from(int64_t cap) {
+        nk = 0;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+            if (keys[s] >= cap) keys[s] = kEmptyKey;
+            nk += keys[s] != kEmptyKey;
+        }
+    }
+};
+
+// SmemKbuf: a ring of K slots per lane in shared memory, laid out slot-major within the warp
+// (slot s of lane l at col[32 s], col = warp base + l), so the 32 lanes of a warp always hit
+// 32 distinct 8-byte words whatever their ring positions: no bank conflicts.  Only the head,
+// the fill and copies of front() and last() live in registers, which frees the 64 registers
+// of the register buffer for occupancy.  An insert shifts the keys after the new one by one
+// slot (insertion order is nearly ascending in best-first order, so shifts are short); a pop
+// advances the head.
+template <int K>
+struct SmemKbuf {
+    static_assert((K & (K - 1)) == 0, "ring size must be a power of two");
+    int64_t* col;
+    int head, nk;
+    int64_t fr, lst;
+    __device__ __forceinline__ explicit SmemKbuf(int64_t* c) : col(c) {}
+    __device__ __forceinline__ int64_t& at(int i) const { return col[((head + i) & (K - 1)) * 32]; }
+    __device__ __forceinline__ void reset() {
+        head = 0;
+        nk = 0;
+        fr = lst = kEmptyKey;
+    }
+    __device__ __forceinline__ int64_t front() const { return fr; }
+    __device__ __forceinline__ int64_t last() const { return lst; }
+    __device__ __forceinline__ void insert_warp(bool ins, int64_t key) {
+        if (!ins) return;
+        int i = nk < K ? nk : K - 1;  // a full ring drops its last key
+        while (i > 0) {
+            const int64_t v = at(i - 1);
+            if (v < key) break;
+            at(i) = v;
+            --i;
+        }
+        at(i) = key;
+        if (nk < K) ++nk;
+        if (i == 0) fr = key;
+        lst = nk == K ? at(K - 1) : kEmptyKey;
+    }
+    __device__ __forceinline__ void pop(unsigned) {
+        head = (head + 1) & (K - 1);
+        --nk;
+        fr = nk > 0 ? at(0) : kEmptyKey;
+        lst = kEmptyKey;
+    }
+    __device__ __forceinline__ void drop_from(int64_t cap) {
+        const int before = nk;
+        while (nk > 0 && at(nk - 1) >= cap) --nk;
+        if (nk == 0) fr = kEmptyKey;
+        if (nk != before) lst = kEmptyKey;
+    }
+};
+
 // One segment of a ray that continues a composite already under way (the scene renderer's
 // segments between surfaces): hits with entry in [t0, end) where cap0 = pack_key(end, 0)
 // (kEmptyKey: no end), ids recorded as id | tag, depth accumulated only when `depth` is set.
@@ -1380,12 +1497,17 @@ struct SegRange {
 
 // SEG = false: a camera ray from scratch (T = 1, nothing composited, entries from t_near).
 // SEG = true: the segment `seg` continues (C, T, depth, count); overflowing ids are reported.
-template <int K, bool COUNT, int W, bool EPS2 = false, bool SEG = false>
+// SMEMK: the pending hits in a shared-memory ring (SmemKbuf; kb_col = this lane's column of
+// its warp's 32 K-slot block) instead of registers.
+template <int K, bool COUNT, int W, bool EPS2 = false, bool SEG = false, bool SMEMK = false>
 __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                  const TraceParams& P, int64_t pix, bool valid, const float3 o, const float3 d,
                                                  float& C0, float& C1, float& C2, float& T, float& depth,
                                                  int64_t& last_key, int& count, Counters& cnt, int* err,
-                                                 const SegRange seg = SegRange{0.f, kEmptyKey, 0, true}) {
+                                                 const SegRange seg = SegRange{0.f, kEmptyKey, 0, true},
+                                                 int64_t* kb_col = nullptr) {
+    using KB = std::conditional_t<SMEMK, SmemKbuf<K>, RegKbuf<K>>;
+    KB kb(kb_col);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
@@ -1413,16 +1535,11 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         }
         if (COUNT && !done) cnt.rounds++;
         bool active = !done;
-        int64_t keys[K];
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            keys[s] = kEmptyKey;
-        }
-        int nk = 0;  // pending keys (slots [0, nk))
+        kb.reset();
         int64_t cap = cap0;
         const float tlo = lo_key < 0 ? tmin : key_t(lo_key);
         auto composite_front = [&]() {
-            const int64_t key = keys[0];
+            const int64_t key = kb.front();
             const int j = key_j(key);
             Hit hc;  // the same solve as at insertion time: the same bits
             ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
@@ -1437,7 +1554,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                 T2 = __fmul_rn(T2, __fsub_rn(1.f, a));
                 lp_key = key;
                 if (T2 < P.eps2) done = true;
-                kbuf_pop_warp<K>(keys, nk, kEmptyKey, __activemask());
+                kb.pop(__activemask());
                 return;
             }
             const float w = __fmul_rn(T, a);
@@ -1454,27 +1571,26 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             if (COUNT) cnt.hits++;
             if (EPS2 && T < eps) ph2 = true;
             else if (T < eps || count >= P.k_max) done = true;
-            kbuf_pop_warp<K>(keys, nk, kEmptyKey, __activemask());
+            kb.pop(__activemask());
         };
-        auto drop_cap = [&](float e) {  // a node with packet entry e was dropped for this pass
+        auto drop_cap = [&](float e) {  // a node with packet entry e was dropped (kept list full)
             if (active) {
                 cap = min(cap, pack_key(fmaxf(e, 0.f), 0));
                 // pending hits at or beyond the new cap may be preceded by hits of the dropped
                 // subtree: give them back (the next pass finds them again)
-                nk = 0;
-#pragma unroll
-                for (int s = 0; s < K; ++s) {
-                    if (keys[s] >= cap) keys[s] = kEmptyKey;
-                    nk += keys[s] != kEmptyKey;
-                }
+                kb.drop_from(cap);
             }
         };
         WarpQueue q;
         wq_init<false>(q);
         wq_push<false>(q, -INF, nodes.root, lane);
+        WarpDefer wd;
+        int wd_n = 0;
+        float wd_best = wd_none<false>();
         uint32_t qtop = wq_extreme_key<false>(q);  // the queue's minimum key, kept across steps
         int visits = 0;
         while (true) {
+            if (qtop == wq_empty<false>() && wd_n > 0) qtop = wd_refill<false>(wd, wd_n, wd_best, q, lane);
             float e_node;
             int node;
             const bool popped = wq_pop_known<false>(q, qtop, e_node, node, lane);
@@ -1482,8 +1598,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             bool need = false;
             if (popped && active) {
                 const float tcap = cap == kEmptyKey ? INF : key_t(cap);
-                const bool full = keys[K - 1] != kEmptyKey;
-                const float tK = full ? key_t(keys[K - 1]) : INF;
+                const int64_t kK = kb.last();
+                const float tK = kK != kEmptyKey ? key_t(kK) : INF;
                 if (e_node <= tcap) {
                     if (e_node > tK) cap = min(cap, pack_key(fmaxf(e_node, 0.f), 0));
                     else need = true;
@@ -1510,8 +1626,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                 }
                 if (need) {
                     const float tcap = cap == kEmptyKey ? INF : key_t(cap);
-                    const bool full = keys[K - 1] != kEmptyKey;
-                    const float tK = full ? key_t(keys[K - 1]) : INF;
+                    const int64_t kK = kb.last();
+                    const float tK = kK != kEmptyKey ? key_t(kK) : INF;
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         h[c] = ch.ref[c] != kEmptyRef && e[c] <= fminf(x[c], tcap);
@@ -1548,8 +1664,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                 if (hh.hit) {
                                     const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
                                     if (key > lo_key && key < cap) {
-                                        if (key < keys[K - 1]) {
-                                            if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
+                                        const int64_t kK = kb.last();
+                                        if (key < kK) {
+                                            if (kK != kEmptyKey) cap = kK;
                                             ins = true;
                                             ikey = key;
                                             if (COUNT) cnt.inserted++;
@@ -1559,7 +1676,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                     }
                                 }
                             }
-                            if (__any_sync(FULL, ins)) kbuf_insert_warp<K>(keys, nk, ins, ikey);
+                            if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
                         }
                     }
                 }
@@ -1568,8 +1685,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                 for (int c = 0; c < W; ++c) in[c] = h[c] && ch.ref[c] >= 0;
                 if (need) {
                     const float tcap = cap == kEmptyKey ? INF : key_t(cap);
-                    const bool full = keys[K - 1] != kEmptyKey;
-                    const float tK = full ? key_t(keys[K - 1]) : INF;
+                    const int64_t kK = kb.last();
+                    const float tK = kK != kEmptyKey ? key_t(kK) : INF;
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         if (in[c] && e[c] > tcap) in[c] = false;
@@ -1580,17 +1697,20 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     }
                 }
                 float ev;
+                int ednode;
 #pragma unroll
                 for (int c = 0; c < W; ++c) {
                     if (__any_sync(FULL, in[c])) {
                         const float ep = warp_min_nonneg(in[c] ? e[c] : INF);  // e >= tlo >= 0
-                        if (wq_push_evict<false>(q, ep, ch.ref[c], lane, ev)) drop_cap(ev);
+                        if (wq_push_displace<false>(q, ep, ch.ref[c], lane, ev, ednode) && !wd_add<false>(wd, wd_n, wd_best, ev, ednode))
+                            drop_cap(ev);
                     }
                 }
             }
             qtop = wq_extreme_key<false>(q);
-            const float bound = wq_key_priority<false>(qtop);  // +inf when empty: composite all pending
-            while (active && !done && keys[0] != kEmptyKey && key_t(keys[0]) < bound) composite_front();
+            // +inf when nothing is left: composite all pending
+            const float bound = fminf(wq_key_priority<false>(qtop), wd_best);
+            while (active && !done && kb.front() != kEmptyKey && key_t(kb.front()) < bound) composite_front();
             active = active && !done;
             if (!popped || !__any_sync(FULL, active)) break;
         }
@@ -1656,7 +1776,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 scatter_grad_warp(gtmp, jout, vout);
             }
         };
-        auto drop_floor = [&](float x) {  // a node with packet exit x was dropped for this pass
+        auto drop_floor = [&](float x) {  // a node with packet exit x was dropped (kept list full)
             if (active) {
                 floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
                 nk = 0;
@@ -1670,11 +1790,16 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         WarpQueue q;
         wq_init<true>(q);
         wq_push<true>(q, INF, nodes.root, lane);
+        WarpDefer wd;
+        int wd_n = 0;
+        float wd_best = wd_none<true>();
+        uint32_t qtop = wq_extreme_key<true>(q);  // the queue's maximum key, kept across steps
         int visits = 0;
         while (true) {
+            if (qtop == wq_empty<true>() && wd_n > 0) qtop = wd_refill<true>(wd, wd_n, wd_best, q, lane);
             float x_node;
             int node;
-            const bool popped = wq_pop<true>(q, x_node, node, lane);
+            const bool popped = wq_pop_known<true>(q, qtop, x_node, node, lane);
             bool need = false;
             if (popped && active) {
                 const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
@@ -1772,15 +1897,19 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     }
                 }
                 float ev;
+                int ednode;
 #pragma unroll
                 for (int c = 0; c < W; ++c) {
                     if (__any_sync(FULL, in[c])) {
                         const float xp = warp_max_nonneg(in[c] ? x[c] : 0.f);  // x >= tfl >= 0
-                        if (wq_push_evict<true>(q, xp, ch.ref[c], lane, ev)) drop_floor(ev);
+                        if (wq_push_displace<true>(q, xp, ch.ref[c], lane, ev, ednode) && !wd_add<true>(wd, wd_n, wd_best, ev, ednode))
+                            drop_floor(ev);
                     }
                 }
             }
-            const float bound = wq_top<true>(q);  // -inf when empty: replay everything pending
+            qtop = wq_extreme_key<true>(q);
+            // -inf when nothing is left: replay everything pending
+            const float bound = fmaxf(wq_key_priority<true>(qtop), wd_best);
             replay_while([&] { return active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound; });
             active = active && remaining > 0;
             if (!popped || !__any_sync(FULL, active)) break;

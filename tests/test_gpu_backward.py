@@ -206,3 +206,14 @@ def test_gradient_through_log_scale_and_logit_activations():
     (rgb.sum() + alpha.sum()).backward()
     assert torch.isfinite(log_s.grad).all() and torch.isfinite(logit.grad).all()
     assert log_s.grad.abs().sum() > 0 and logit.grad.abs().sum() > 0
+
+
+def test_gradients_rays_starting_inside_many_overlapping_boxes():
+    """The dense-overlap case of the forward tests: the re-traversing adjoint's queue overflows
+    too (hit_list 0), and hit lists shorter than the rays mix replay and re-traversal."""
+    from paper_2501_19196_gb300 import native
+    from test_gpu_forward import dense_overlap_case
+    sc, cams = dense_overlap_case()
+    for tune in (dict(), dict(hit_list=0), dict(hit_list=64)):
+        errs, bad = _grad_case(sc, cams, params(eps1=1e-4), tune=native.default_tune(**tune))
+        assert max(errs.values()) < TOL_GRAD, (tune, errs)

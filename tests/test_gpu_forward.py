@@ -306,3 +306,30 @@ def test_invalid_render_arguments_are_rejected():
     r.render(cam, params(Q=4.0))
     r.check_device()
     r.close()
+
+
+# ------------------------------------------------------------------------------------------
+# rays that start among many overlapping boxes (best-first queue overflow)
+# ------------------------------------------------------------------------------------------
+def dense_overlap_case(seed=11, n=3000):
+    """A camera inside a cloud of large, faint Gaussians: every ray starts inside most of the
+    tree's boxes, so the best-first queue (128 entries) overflows with nodes whose entry lies at
+    the pass's start, and a ray needs hundreds of hits (many passes of K)."""
+    rng = np.random.default_rng(seed)
+    sc = scenes.Scene(rng.uniform(-1, 1, (n, 3)).astype(np.float32), rng.standard_normal((n, 4)).astype(np.float32),
+                      np.exp(rng.normal(np.log(0.35), 0.2, (n, 3))).astype(np.float32),
+                      rng.uniform(0.01, 0.05, n).astype(np.float32), rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    cams = scenes.look_at_camera((0.05, 0.02, -0.1), (0.0, 0.0, 1.0), 24, 16, 70.0)
+    return sc, cams
+
+
+def test_rays_starting_inside_many_overlapping_boxes():
+    from paper_2501_19196_gb300 import native
+    sc, cams = dense_overlap_case()
+    prm = params(eps1=1e-4)
+    cam, px, py = scenes.pixel_grid(cams)
+    ora = oracle_pixels(sc, cams, cam, px, py, prm)
+    assert np.median(ora["n_hits"]) > 200  # several passes of K = 32 per ray
+    for tune in (dict(), dict(traversal=1), dict(kbuf=8)):
+        g = gpu_render(sc, cams, prm, tune=native.default_tune(**tune))  # raises on a loop-guard error
+        compare_image(g, ora, pixel_index(cams, cam, px, py), label=f"dense overlap {tune}")
