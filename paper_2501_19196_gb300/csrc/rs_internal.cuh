@@ -184,6 +184,59 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
     }
 }
 
+// The closest-approach geometry of the adjoint (p = M v and v, as ray_ellipsoid<true> gives
+// them) to full FP32 accuracy.  In the solve above p = o' + tm d' is a difference of terms of
+// size |M (o - m)|, which exceeds |p| by up to five digits for a Gaussian a thousand times
+// thinner along one axis than along the others; the component of p along that axis, which the
+// gradient scales by 1/s, then keeps few correct digits.  Here the solve is re-centred at
+// tstar, the forward's parameter of the closest point: w = (o - m) + tstar d is formed as an
+// unevaluated pair wh + wl from exact differences (two_sum) and exact products (an FMA gives
+// the rounding error of a product), M w by compensated dot products (Ogita, Rump and Oishi's
+// Dot2), and the small remaining offset along d' is removed by one projection.  alpha still
+// comes from the forward's D2, so its bits do not change.
+__device__ __forceinline__ void closest_point_accurate(const float3 o, const float3 d, const float4 r0,
+                                                       const float4 r1, const float4 r2, float tstar, float p[3],
+                                                       float v[3]) {
+    const float m[3] = {r0.w, r1.w, r2.w};
+    const float oo[3] = {o.x, o.y, o.z};
+    const float dd[3] = {d.x, d.y, d.z};
+    float wh[3], wl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float eh, el, sh, se;
+        two_sum(oo[k], -m[k], eh, el);  // o - m = eh + el exactly
+        const float ph = __fmul_rn(tstar, dd[k]);
+        const float pl = __fmaf_rn(tstar, dd[k], -ph);  // tstar d = ph + pl exactly
+        two_sum(eh, ph, sh, se);
+        two_sum(sh, __fadd_rn(__fadd_rn(se, el), pl), wh[k], wl[k]);
+    }
+    const float Mr[3][3] = {{r0.x, r0.y, r0.z}, {r1.x, r1.y, r1.z}, {r2.x, r2.y, r2.z}};
+    float q[3], dp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float sum = 0.f, err = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float pr = __fmul_rn(Mr[k][i], wh[i]);
+            const float pe = __fmaf_rn(Mr[k][i], wh[i], -pr);
+            float t, e;
+            two_sum(sum, pr, t, e);
+            sum = t;
+            err = __fmaf_rn(Mr[k][i], wl[i], __fadd_rn(err, __fadd_rn(e, pe)));
+        }
+        q[k] = __fadd_rn(sum, err);  // (M w)_k
+        dp[k] = __fmaf_rn(Mr[k][2], dd[2], __fmaf_rn(Mr[k][1], dd[1], __fmul_rn(Mr[k][0], dd[0])));
+    }
+    const float a = __fmaf_rn(dp[2], dp[2], __fmaf_rn(dp[1], dp[1], __fmul_rn(dp[0], dp[0])));
+    const float b = __fmaf_rn(q[2], dp[2], __fmaf_rn(q[1], dp[1], __fmul_rn(q[0], dp[0])));
+    const float tau = -__fdiv_rn(b, a);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fmaf_rn(tau, dp[k], q[k]);
+        v[k] = __fadd_rn(__fmaf_rn(tau, dd[k], wh[k]), wl[k]);
+    }
+}
+
 // The ordering parameter of a hit: its entry t1, or (sort key 1) the parameter of the maximum
 // response, which is never below t1 (the max guards FP32 rounding at grazing incidence).
 __device__ __forceinline__ float hit_key_t(const Hit& h, int sort_key) {

@@ -398,7 +398,8 @@ __device__ __forceinline__ void alpha_to_params(const float4* __restrict__ rec, 
     const float4 g0 = __ldg(rec + 4 * j + 0), g1 = __ldg(rec + 4 * j + 1), g2 = __ldg(rec + 4 * j + 2);
     const float4 sh = __ldg(rec + 4 * j + 3);
     Hit h;
-    ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, tmin, h);
+    ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, tmin, h);
+    closest_point_accurate(o, d, g0, g1, g2, h.tm, h.p, h.v);
     const float e = expf(__fmul_rn(-0.5f, h.D2));
     const float a = __fmul_rn(sh.x, e);
     const float gD2 = -0.5f * a * dLda;

@@ -344,7 +344,8 @@ __device__ __forceinline__ void adjoint_hit(const float4* __restrict__ rec, int 
     const float4 g2 = __ldg(rec + 4 * j + 2);
     const float4 sh = __ldg(rec + 4 * j + 3);
     Hit h;
-    ray_ellipsoid<true>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+    ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
+    closest_point_accurate(o, d, g0, g1, g2, h.tm, h.p, h.v);
     const float tk = DEPTH ? hit_key_t(h, P.sort_key) : 0.f;
     const float e = expf(__fmul_rn(-0.5f, h.D2));
     const float a = __fmul_rn(sh.x, e);
