@@ -1222,10 +1222,12 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
 // every lane: forward, no undiscovered hit of any lane precedes it, and pending hits nearer
 // than it are composited at once; the adjoint mirrors this back to front.  Hits therefore
 // leave the pending buffer almost as soon as they are found and one pass usually suffices.
-// A full queue drops the new node and caps (floors) the keys of every active lane, which
-// keeps the result exact at the cost of a further pass.
+// The queue holds 64 nodes (2 slots per lane; 4 slots measured 7 % slower).  A node displaced
+// from the full queue goes to a per-warp list and returns later in the same pass; only when
+// that list is full too is a node dropped, capping (flooring) the keys of every active lane,
+// which keeps the result exact at the cost of a further pass.
 // ---------------------------------------------------------------------------------------------
-constexpr int kQSlots = 4;
+constexpr int kQSlots = 2;
 
 // Each occupied slot holds one 32-bit key: the priority's FP32 bit pattern with its 7 low
 // mantissa bits replaced by the slot's warp-wide id (lane * kQSlots + slot).  Priorities are
@@ -1355,13 +1357,15 @@ __device__ __forceinline__ bool wq_push_displace(WarpQueue& q, float pr, int nod
 
 // Nodes displaced from a full queue, kept for later in the same pass.  Dropping such a node
 // instead caps the pass at its priority, and when no hit lies between the pass's start and
-// that priority the pass composites nothing and the next one repeats it exactly: a live lock
-// on rays that start among many overlapping boxes (reflected rays inside the cloud).  The list
-// is warp-uniform (every lane holds the same entries); only a full list drops a node.
-// The list's entries live in local memory (touched only when the queue is full); its fill n and
-// its best priority (smallest for the min-queue, largest for the max-queue, +-inf when empty)
-// are kept by the caller in registers.
-constexpr int kDeferSlots = 64;
+// that priority the pass composites nothing; the next pass then starts at the cap (the
+// forward's progress rule), but a cap at the pass's start itself, from nodes all entered at
+// that point, would repeat the pass until the loop guard ends it.  Such frontiers arise on rays
+// that start among many overlapping boxes (reflected rays inside the cloud).  The list is
+// warp-uniform (every lane holds the same entries); only a full list drops a node.  Its
+// entries live in local memory (touched only when the queue is full); its fill n and its best
+// priority (smallest for the min-queue, largest for the max-queue, +-inf when empty) are kept
+// by the caller in registers.
+constexpr int kDeferSlots = 448;
 struct WarpDefer {
     int node[kDeferSlots];
     float pr[kDeferSlots];
@@ -1536,6 +1540,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         }
         if (COUNT && !done) cnt.rounds++;
         bool active = !done;
+        const int64_t pass_last = EPS2 ? lp_key : last_key;  // last key composited before this pass
         kb.reset();
         int64_t cap = cap0;
         const float tlo = lo_key < 0 ? tmin : key_t(lo_key);
@@ -1716,8 +1721,15 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             if (!popped || !__any_sync(FULL, active)) break;
         }
         if (active && !done) {
-            if (cap == cap0) done = true;  // nothing was dropped: every hit before the end is in
-            else lo_key = EPS2 ? lp_key : last_key;
+            if (cap == cap0) {
+                done = true;  // nothing was dropped: every hit before the end is in
+            } else {
+                const int64_t got = EPS2 ? lp_key : last_key;
+                // A pass that composited nothing ended with an empty buffer: no hit after lo_key
+                // lies below the cap (explored nodes would have given it, dropped or pruned
+                // ones hold none below the cap), so the next pass may start at the cap.
+                lo_key = got != pass_last ? got : max(lo_key, cap - 1);
+            }
         }
     }
     if (EPS2 && valid)
