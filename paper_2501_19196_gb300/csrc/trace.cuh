@@ -89,6 +89,80 @@ __device__ __forceinline__ uint32_t leaf_sphere_mask(const float4* __restrict__ 
     return mask;
 }
 
+// The rays of a warp that share one origin (a camera's tile) as a cone: axis, cos and sin of
+// the half-angle, widened so that rounding cannot make it narrower than the rays.
+struct RayCone {
+    float3 ax;
+    float cth, sth;
+    bool ok;  // every lane has the same origin
+};
+
+__device__ __forceinline__ RayCone warp_ray_cone(const float3 o, const float3 d) {
+    const unsigned FULL = 0xffffffffu;
+    RayCone c;
+    const float ox = __shfl_sync(FULL, o.x, 0), oy = __shfl_sync(FULL, o.y, 0), oz = __shfl_sync(FULL, o.z, 0);
+    c.ok = __all_sync(FULL, o.x == ox && o.y == oy && o.z == oz);
+    float sx = d.x, sy = d.y, sz = d.z;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        sx += __shfl_xor_sync(FULL, sx, m);
+        sy += __shfl_xor_sync(FULL, sy, m);
+        sz += __shfl_xor_sync(FULL, sz, m);
+    }
+    const float il = rsqrtf(fmaxf(sx * sx + sy * sy + sz * sz, 1e-30f));
+    c.ax = make_float3(sx * il, sy * il, sz * il);
+    // per lane: cos and sin of the angle to the axis (the sine from the cross product, which
+    // keeps its accuracy for narrow cones)
+    const float cs = d.x * c.ax.x + d.y * c.ax.y + d.z * c.ax.z;
+    const float cx = d.y * c.ax.z - d.z * c.ax.y, cy = d.z * c.ax.x - d.x * c.ax.z, cz = d.x * c.ax.y - d.y * c.ax.x;
+    const float sn = sqrtf(cx * cx + cy * cy + cz * cz);
+    float mc = cs;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) mc = fminf(mc, __shfl_xor_sync(FULL, mc, m));
+    c.cth = fmaxf(mc - 1e-5f, -1.f);
+    c.sth = fminf(__uint_as_float(__reduce_max_sync(FULL, __float_as_uint(sn))) + 1e-5f, 1.f);
+    c.ok = c.ok && c.cth > 0.f;  // narrower than a half space
+    return c;
+}
+
+// leaf_sphere_mask behind a cone pre-test: lane g tests sphere start + g against the warp's ray
+// cone, and only the spheres the cone may reach get the per-lane test (same result: the cone
+// test is conservative and the per-lane test decides).  A sphere (c, r) can meet a ray of the
+// cone at t >= 0 only if the origin lies inside it, or its centre is ahead (<w, axis> > -r) and
+// its distance to the cone's surface, |w x axis| cos - <w, axis> sin, is at most r.
+__device__ __forceinline__ uint32_t leaf_sphere_mask_cone(const float4* __restrict__ sph, int start, int num,
+                                                          bool want, const float3 o, const float3 d,
+                                                          const RayCone& cone) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float4 mine = make_float4(0.f, 0.f, 0.f, -1.f);
+    bool reach = false;
+    if (lane < num) {
+        mine = __ldg(sph + start + lane);
+        const float wx = mine.x - o.x, wy = mine.y - o.y, wz = mine.z - o.z;
+        const float L2 = wx * wx + wy * wy + wz * wz;
+        const float r = sqrtf(mine.w) * 1.0001f + 1e-6f * sqrtf(L2);
+        const float t = wx * cone.ax.x + wy * cone.ax.y + wz * cone.ax.z;
+        const float cx = wy * cone.ax.z - wz * cone.ax.y, cy = wz * cone.ax.x - wx * cone.ax.z;
+        const float cz = wx * cone.ax.y - wy * cone.ax.x;
+        const float dperp = sqrtf(cx * cx + cy * cy + cz * cz);
+        reach = L2 <= r * r || (t > -r && dperp * cone.cth - t * cone.sth <= r);
+    }
+    uint32_t cand = __ballot_sync(FULL, reach);
+    uint32_t mask = 0;
+    while (cand) {
+        const int g = __ffs(cand) - 1;
+        cand &= cand - 1;
+        float4 sp;
+        sp.x = __shfl_sync(FULL, mine.x, g);
+        sp.y = __shfl_sync(FULL, mine.y, g);
+        sp.z = __shfl_sync(FULL, mine.z, g);
+        sp.w = __shfl_sync(FULL, mine.w, g);
+        if (want && sphere_may_hit(o, d, sp)) mask |= 1u << g;
+    }
+    return mask;
+}
+
 // The children of one node as seen by the traversal: W = 2 reads a binary node (possibly staged
 // in shared memory), W = 4 a wide node (the node's grandchildren; empty slots have ref kEmptyRef).
 template <int W>
@@ -1516,6 +1590,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    RayCone cone;
+    cone.ok = false;
+    if (!SEG) cone = warp_ray_cone(o, d);  // camera rays share their origin
     const float eps = fmaxf(P.eps1, 1e-30f);
     const float INF = __int_as_float(0x7f800000);
     const float tmin = SEG ? seg.t0 : P.t_near;
@@ -1651,7 +1728,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
                         // sphere pre-test of the whole leaf, then one full test per Gaussian that
                         // some lane may hit (in order: the same inserts as a sequential scan)
-                        const uint32_t mask = leaf_sphere_mask(sph, start, num, want, o, d);
+                        const uint32_t mask = cone.ok ? leaf_sphere_mask_cone(sph, start, num, want, o, d, cone)
+                                                      : leaf_sphere_mask(sph, start, num, want, o, d);
                         uint32_t todo = __reduce_or_sync(FULL, mask);
                         while (todo) {
                             const int g = __ffs(todo) - 1;
