@@ -217,3 +217,21 @@ def test_gradients_rays_starting_inside_many_overlapping_boxes():
     for tune in (dict(), dict(hit_list=0), dict(hit_list=64)):
         errs, bad = _grad_case(sc, cams, params(eps1=1e-4), tune=native.default_tune(**tune))
         assert max(errs.values()) < TOL_GRAD, (tune, errs)
+
+
+def test_ring_16_cameras_full_size_sampled():
+    """The benchmark's workload at full size (1M Gaussians, 16 ring cameras of mixed resolution,
+    12.04M rays) in the batched persistent launch with hit lists: sampled pixels of every camera
+    against the oracle, the image and, with an upstream gradient on those pixels only, every
+    gradient array."""
+    wl = scenes.workload(4)
+    prm = params(eps1=wl.eps1, background=wl.background)
+    cam, px, py = scenes.pixel_grid(wl.cams, stride=173)
+    g = gpu_render(wl.scene, wl.cams, prm)
+    ora = oracle_pixels(wl.scene, wl.cams, cam, px, py, prm)
+    from gpu_util import compare_image
+    err, masked = compare_image(g, ora, pixel_index(wl.cams, cam, px, py), label="16 cameras sampled")
+    errs, bad = _grad_case(wl.scene, wl.cams, prm, stride=173)
+    print(f"16 cameras sampled: pixels {len(cam)}, image err {err:.2e}, gradient rel-L2",
+          {k: f"{v:.2e}" for k, v in errs.items()}, f"flagged {bad:.4f}")
+    assert max(errs.values()) < TOL_GRAD, errs
