@@ -139,7 +139,8 @@ typedef struct {
 /* Tunables.  None changes a result (tests check this), only speed.
  *   tile_w, tile_h  ray tile handled by one warp; tile_w * tile_h == 32
  *   kbuf            per-ray k-buffer depth: 8, 16 or 32
- *   leaf_size       BVH leaf size 1..16 (used by rs_build_accel)
+ *   leaf_size       BVH leaf size 1..32 (used by rs_build_accel); a warp pre-tests a leaf
+ *                   with one bounding sphere per lane
  *   morton_bits     10 (30-bit codes) or 21 (63-bit codes) bits per axis, or 20: extended
  *                   63-bit codes, 20 bits per axis plus a 3-bit size class (from the exponent
  *                   of the largest scale) below the top four levels
@@ -198,7 +199,7 @@ int32_t rs_abi_version(void);
 /* Message of the last failed call on this host thread ("" if none). */
 const char* rs_last_error(void);
 
-/* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 16, 63-bit codes,
+/* Fill *out with the default tunables (8x4 tiles, kbuf 32, leaf 32, 63-bit codes,
  * persistent launch, 4 warps per CTA, best-first warp-packet traversal, 256 staged nodes,
  * hit lists of 256 ids per ray). */
 rs_status rs_default_tune(rs_tune_params* out);

@@ -77,8 +77,8 @@ static rs_status check_tune(const rs_tune_params* t, bool build) {
         return set_error(RS_ERR_INVALID_ARG, "tile %dx%d: tile_w * tile_h must be 32", t->tile_w, t->tile_h);
     if (t->kbuf != 8 && t->kbuf != 16 && t->kbuf != 32)
         return set_error(RS_ERR_INVALID_ARG, "kbuf %d: must be 8, 16 or 32", t->kbuf);
-    if (build && (t->leaf_size < 1 || t->leaf_size > 16))
-        return set_error(RS_ERR_INVALID_ARG, "leaf_size %d: must be 1..16", t->leaf_size);
+    if (build && (t->leaf_size < 1 || t->leaf_size > 32))
+        return set_error(RS_ERR_INVALID_ARG, "leaf_size %d: must be 1..32", t->leaf_size);
     if (build && t->morton_bits != 10 && t->morton_bits != 20 && t->morton_bits != 21)
         return set_error(RS_ERR_INVALID_ARG, "morton_bits %d: must be 10, 20 (extended) or 21", t->morton_bits);
     if (t->block_warps < 1 || t->block_warps > 4)
@@ -119,7 +119,7 @@ rs_status rs_default_tune(rs_tune_params* out) {
     out->tile_w = 8;
     out->tile_h = 4;
     out->kbuf = 32;
-    out->leaf_size = 16;
+    out->leaf_size = 32;
     out->morton_bits = 21;
     out->persistent = 1;
     out->block_warps = 4;

@@ -108,7 +108,7 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     if (n_cams < 1 || n_cams > kCams)
         return set_error(RS_ERR_INVALID_ARG, "%d cameras: the fixed scratch holds 1..%d", n_cams, kCams);
     if (tune->tile_w < 1 || tune->tile_w > 32 || (32 % tune->tile_w) != 0 || tune->tile_h != 32 / tune->tile_w ||
-        (tune->kbuf != 8 && tune->kbuf != 16 && tune->kbuf != 32) || tune->leaf_size < 1 || tune->leaf_size > 16 ||
+        (tune->kbuf != 8 && tune->kbuf != 16 && tune->kbuf != 32) || tune->leaf_size < 1 || tune->leaf_size > 32 ||
         (tune->morton_bits != 10 && tune->morton_bits != 20 && tune->morton_bits != 21) || tune->block_warps < 1 ||
         tune->block_warps > 4 || tune->traversal < 0 || tune->traversal > 2 || tune->smem_nodes < 0 ||
         tune->smem_nodes > kMaxSmemNodes)

@@ -70,7 +70,7 @@ __device__ __forceinline__ int leaf_count(const NodeSrc& ns, int start, int cnt)
 
 // Bounding-sphere pre-test of one leaf for the whole warp: the leaf's spheres are loaded once
 // (lane i holds Gaussian start + i) and broadcast by shuffles.  Bit g of the result is set when
-// this lane wants the leaf and its ray may hit Gaussian start + g.  num <= 32 (leaf_size <= 16).
+// this lane wants the leaf and its ray may hit Gaussian start + g.  num <= 32 (leaf_size <= 32).
 __device__ __forceinline__ uint32_t leaf_sphere_mask(const float4* __restrict__ sph, int start, int num, bool want,
                                                      const float3 o, const float3 d) {
     const unsigned FULL = 0xffffffffu;

@@ -23,7 +23,7 @@ def default_cache_path() -> str:
     return os.environ.get(CACHE_ENV, os.path.join(os.path.expanduser("~"), ".cache", "raysplats_tune.json"))
 
 
-def candidates(tiles=((8, 4), (4, 8)), kbufs=(16, 32), leaves=(8, 16), warps=(4,), morton=(20, 21),
+def candidates(tiles=((8, 4), (4, 8)), kbufs=(16, 32), leaves=(16, 32), warps=(4,), morton=(20, 21),
                traversal=(2,), persistent=1, hit_lists=(256,), smem_nodes=256):
     """The cross product of the given tunables (all persistent launches by default)."""
     out = []

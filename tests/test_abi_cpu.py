@@ -49,7 +49,7 @@ def test_abi_version_and_default_tune(lib):
     assert lib.rs_abi_version() == 1
     t = native.default_tune()
     assert (t.tile_w, t.tile_h, t.kbuf, t.leaf_size, t.morton_bits, t.traversal, t.hit_list) == \
-        (8, 4, 32, 16, 21, 2, 256)
+        (8, 4, 32, 32, 21, 2, 256)
 
 
 def test_host_validation_rejects_bad_arguments(lib):
@@ -65,7 +65,7 @@ def test_host_validation_rejects_bad_arguments(lib):
         native.RS_ERR_INVALID_ARG
     # bad tile / kbuf / leaf / Q_box
     g = native.RsGaussians(10, 16, 16, 16, 16, 16)
-    for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("morton_bits", 7), ("block_warps", 9),
+    for field, val in (("tile_w", 3), ("kbuf", 12), ("leaf_size", 0), ("leaf_size", 33), ("morton_bits", 7), ("block_warps", 9),
                        ("traversal", 4), ("smem_nodes", 513), ("hit_list", -1), ("hit_list", 4097)):
         bad = native.default_tune(**{field: val})
         if field == "tile_w":
