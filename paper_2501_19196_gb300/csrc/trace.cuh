@@ -1590,9 +1590,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
-    RayCone cone;
-    cone.ok = false;
-    if (!SEG) cone = warp_ray_cone(o, d);  // camera rays share their origin
+    // camera rays (and a scene's first segment) share their origin; otherwise cone.ok is false
+    const RayCone cone = warp_ray_cone(o, d);
     const float eps = fmaxf(P.eps1, 1e-30f);
     const float INF = __int_as_float(0x7f800000);
     const float tmin = SEG ? seg.t0 : P.t_near;
