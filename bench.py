@@ -580,6 +580,19 @@ def run_ours(args):
     # forward; adjoint: list replay + re-traversal of the overflow tiles (or one re-traversal
     # launch without hit lists) + finalize
     gpu_launches = args.steps * (launches_build + 1 + (3 if tune_b.hit_list > 0 else 2))
+    # ALU side of the forward (secondary): the FP32 lane operations the traversal must execute
+    # per launch (a model: 30 per node visit for its two slab tests, 55 per full Gaussian test
+    # for the stable solve with its division, 60 per composited hit for the solve again, exp
+    # and the blend; an FMA counts once), against the FP32 lane rate at the sampled SM clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_ops = 30 * sf["nodes_visited"] + 55 * sf["gaussians_tested"] + 60 * sf["hits_composited"]
+    alu_peak = sms * 128 * mhz * 1e6 / 1e12
+    roofline["alu_secondary"] = {
+        "fp32_ops_per_launch": fp32_ops, "achieved": fp32_ops / (kms["fwd"] * 1e-3) / 1e12, "peak": alu_peak,
+        "unit": "T FP32 lane ops/s", "frac": fp32_ops / (kms["fwd"] * 1e-3) / 1e12 / alu_peak,
+        "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
+        "kernel": "k_render_fwd (persistent)"}
     value = P / ms_fb / 1e3 * world
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
