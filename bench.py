@@ -68,6 +68,23 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(ms, world, device="cpu"):
+    """The job's time per step: the slowest rank's (every rank times the same steps between two
+    barriers).  One rank: the time itself."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mrays_s(rays_per_rank, ms, world):
+    """Whole-job throughput: the rays all ranks processed per step over the job's time per step."""
+    return rays_per_rank * world / ms / 1e3
+
+
 def src_hash(names=KERNEL_SOURCES):
     h = hashlib.sha256()
     for name in names:
@@ -362,6 +379,7 @@ def run_ours(args):
     def timed(fn, steps, warmup, sampler=None):
         for _ in range(warmup):
             fn()
+        torch.cuda.synchronize()
         barrier()
         if sampler:
             sampler.start()
@@ -373,13 +391,10 @@ def run_ours(args):
             fn()
             e1.record(stream)
             evs.append((e0, e1))
+        torch.cuda.synchronize()
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, world, dev)
         return ms, clocks
 
     if args.profile:
@@ -523,8 +538,8 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         barrier()
-        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
-        e2e = {"value": P / ms_e2e / 1e3 * world, "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
+        ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
+        e2e = {"value": job_mrays_s(P, ms_e2e, world), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
                "path": "pinned host params + dL -> device, graph replay, gradients -> pinned host"}
 
@@ -593,7 +608,7 @@ def run_ours(args):
         "unit": "T FP32 lane ops/s", "frac": fp32_ops / (kms["fwd"] * 1e-3) / 1e12 / alu_peak,
         "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (sampled)",
         "kernel": "k_render_fwd (persistent)"}
-    value = P / ms_fb / 1e3 * world
+    value = job_mrays_s(P, ms_fb, world)
     line = {
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
