@@ -1842,6 +1842,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         }
         int nk = 0;  // pending keys (slots [0, nk))
         int64_t floor_key = -1;
+        const int64_t pass_hi = hi_key;  // where this pass starts (from the back)
         const float thi = key_t(hi_key);
         bool stop = false;
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
@@ -2009,6 +2010,9 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             atomicOr(err, kErrReplayMismatch);
             remaining = 0;
         }
+        // a pass that replayed nothing ended with an empty buffer: every remaining hit lies at
+        // or below its floor, so the next pass may start there (the forward's progress rule)
+        if (active && remaining > 0 && hi_key == pass_hi) hi_key = min(hi_key, floor_key + 1);
     }
 }
 
