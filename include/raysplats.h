@@ -138,7 +138,8 @@ typedef struct {
 
 /* Tunables.  None changes a result (tests check this), only speed.
  *   tile_w, tile_h  ray tile handled by one warp; tile_w * tile_h == 32
- *   kbuf            per-ray k-buffer depth: 8, 16 or 32
+ *   kbuf            per-ray k-buffer depth: 8, 16 or 32 (with traversal 2 and 32, the
+ *                   forward keeps it in shared memory instead of registers)
  *   leaf_size       BVH leaf size 1..32 (used by rs_build_accel); a warp pre-tests a leaf
  *                   with one bounding sphere per lane
  *   morton_bits     10 (30-bit codes) or 21 (63-bit codes) bits per axis, or 20: extended
@@ -153,7 +154,8 @@ typedef struct {
  *                   distributed over the warp's registers); 3: as 2 over 4-wide nodes (each
  *                   binary node's grandchildren; rs_build_accel builds them when given 3)
  *   smem_nodes      0..512: the top BVH nodes (breadth first) that rs_build_accel stages for
- *                   the render kernels' shared memory (64 B each); 0 disables staging
+ *                   the render kernels' shared memory (64 B each); 0 disables staging.  The
+ *                   forward with its k-buffer in shared memory does not use them
  *   hit_list        0..4096: rs_render records the sorted ids of each ray's first hit_list
  *                   composited hits (4 B each, hit_list * 4 B per ray in the state), and the
  *                   adjoint replays every ray with at most hit_list hits from that list instead
