@@ -267,20 +267,24 @@ rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int
                   rs_tune_params* best, float* ms_out, void* cuda_stream);
 
 /* ---- Fixed-scratch render (no counterpart in the paper) ----------------------------------
- * For callers that cannot allocate device memory -- code that runs while a CUDA graph is being
- * captured under a no-allocation policy, plug-ins whose host application owns every device
- * allocation, tools that must not grow the process's memory -- this entry point builds the
- * acceleration structure and renders the cameras (the work of rs_build_accel + rs_render)
- * without any cudaMalloc, cudaFree or other allocating call.  Every intermediate lives in one
- * file-scope device array of fixed size (about 12 MB, held by every GPU that loads the
- * library until the process exits).  The caller still passes the scene, the cameras and the
- * output buffers; there is no per-ray state for a backward pass.
+ * For callers that cannot allocate device memory -- plug-ins whose host application owns every
+ * device allocation (they are handed buffers, not an allocator), and tools that run under a
+ * fixed device-memory budget and must not grow the process's footprint -- this entry point
+ * builds the acceleration structure and renders the cameras (the work of rs_build_accel +
+ * rs_render) without any cudaMalloc, cudaFree or other allocating call.  Every intermediate
+ * lives in one file-scope device array of fixed size (about 12 MB, held by every GPU that
+ * loads the library until the process exits).  The caller still passes the scene, the cameras
+ * and the output buffers; there is no per-ray state for a backward pass.
  *   - Limits: g->n <= RS_FIXED_MAX_GAUSSIANS, n_cams <= RS_FIXED_MAX_CAMERAS, sum of W*H <=
- *     RS_FIXED_MAX_PIXELS; larger requests return RS_ERR_INVALID_ARG before any launch.
+ *     RS_FIXED_MAX_PIXELS (each camera is checked on its own first); larger requests, and
+ *     non-finite camera or render parameters, return RS_ERR_INVALID_ARG before any launch.
  *   - The first call on a device resolves the array's device address (set-up, once per
- *     device, with that device current); make it before any stream capture.
+ *     device, with that device current) and caches it; make that first call before any
+ *     stream capture, and make no call on a device after a cudaDeviceReset of it.
  *   - All calls share the array and it keeps the previous call's contents (the call clears
  *     what must start at zero): calls that overlap on the GPU race with each other.
+ *   - The camera table is passed to the device as a kernel argument: no host buffer is read
+ *     after the call returns.
  *   - Q plays the role of rs_build_accel's Q_box.  Device consistency checks are not reported
  *     (there is no handle to query). */
 #define RS_FIXED_MAX_GAUSSIANS 32768

@@ -1,19 +1,22 @@
 // fixed_scratch.cu -- rs_render_fixed_scratch: a build + forward render that allocates nothing.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being captured with a
-// strict allocation policy, plug-ins whose host application owns every device allocation, or
-// tools that must not grow the process's memory footprint.  This entry point serves them: it
-// takes the caller's scene, cameras and output buffers and keeps every intermediate (render
-// records, boxes, sort buffers, tree, nodes, camera table, work counter, per-ray state) in one
-// file-scope __device__ array of fixed size, shared by all calls on a device.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns every device
+// allocation (the plug-in gets buffers, never an allocator), and tools that run under a fixed
+// device-memory budget and must not grow the process's footprint.  This entry point serves
+// them: it takes the caller's scene, cameras and output buffers and keeps every intermediate
+// (render records, boxes, sort buffers, tree, nodes, camera table, work counter, per-ray state)
+// in one file-scope __device__ array of fixed size, shared by all calls on a device.
 //
 // Limits: n <= RS_FIXED_MAX_GAUSSIANS, sum of W*H <= RS_FIXED_MAX_PIXELS, n_cams <=
 // RS_FIXED_MAX_CAMERAS; the array is about 12 MB and every GPU that loads the library holds
 // it until the process exits.  The first call on a device resolves the array's device address
-// (cudaGetSymbolAddress with that device current); make that first call before any stream
-// capture.  Calls share the array and keep the previous call's contents, so calls that overlap
-// on the GPU (different streams, or different host threads on the same device) race; the
-// entry point itself clears everything that must start at zero.
+// (cudaGetSymbolAddress with that device current) and caches it for the life of the process;
+// make that first call before any stream capture, and do not call the entry point again on a
+// device after cudaDeviceReset (the cached address belongs to the context that was reset).
+// Calls share the array and keep the previous call's contents, so calls that overlap on the
+// GPU (different streams, or different host threads on the same device) race; the entry point
+// itself clears everything that must start at zero.  The camera table travels as a kernel
+// argument, so no host memory is read after the call returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -70,6 +73,16 @@ constexpr int kMaxDevices = 64;
 static unsigned char* g_base[kMaxDevices] = {};
 static std::mutex g_mu;
 
+// The camera table, passed by value to a one-block kernel that writes it into the array.
+struct CamTable {
+    DevCam c[kCams];
+};
+static_assert(sizeof(CamTable) <= 4000, "the camera table must fit in a kernel's parameters");
+
+__global__ void k_upload_cams(const CamTable t, int n, DevCam* __restrict__ dst) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = t.c[i];
+}
+
 // device address of g_scratch on the current device (resolved once per device)
 static rs_status scratch_base(unsigned char** out) {
     int dev = 0;
@@ -118,13 +131,25 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
         return set_error(RS_ERR_INVALID_ARG, "bad render parameters");
     if (p->depth_mode != 0) return set_error(RS_ERR_UNSUPPORTED, "only depth_mode 0 is implemented");
     if (p->sort_key != 0 && p->sort_key != 1) return set_error(RS_ERR_INVALID_ARG, "sort_key must be 0 or 1");
-    DevCam table[kCams];
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(p->background[k])) return set_error(RS_ERR_INVALID_ARG, "background must be finite");
+    CamTable table;
+    memset(&table, 0, sizeof(table));
     int64_t tiles = 0, pix = 0;
     for (int c = 0; c < n_cams; ++c) {
         const rs_camera& C = cams[c];
-        if (C.width < 1 || C.height < 1 || C.fx == 0.f || C.fy == 0.f)
-            return set_error(RS_ERR_INVALID_ARG, "camera %d: bad size or focal length", c);
-        DevCam& D = table[c];
+        // each camera on its own first, so that no running total can overflow
+        if (C.width < 1 || C.height < 1 || C.width > kPix || C.height > kPix ||
+            (int64_t)C.width * C.height > kPix - pix)
+            return set_error(RS_ERR_INVALID_ARG,
+                             "camera %d: %dx%d pixels (after %lld): the fixed scratch holds at most %lld pixels", c,
+                             C.width, C.height, (long long)pix, (long long)kPix);
+        bool ok = std::isfinite(C.fx) && std::isfinite(C.fy) && std::isfinite(C.cx) && std::isfinite(C.cy) &&
+                  C.fx != 0.f && C.fy != 0.f;
+        for (int k = 0; k < 9; ++k) ok = ok && std::isfinite(C.R_wc[k]);
+        for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(C.pos[k]);
+        if (!ok) return set_error(RS_ERR_INVALID_ARG, "camera %d: non-finite or zero-focal parameters", c);
+        DevCam& D = table.c[c];
         memcpy(D.R, C.R_wc, sizeof(D.R));
         memcpy(D.pos, C.pos, sizeof(D.pos));
         D.fx = C.fx;
@@ -140,9 +165,6 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
         tiles += (int64_t)D.tiles_x * D.tiles_y;
         pix += (int64_t)C.width * C.height;
     }
-    if (pix > kPix)
-        return set_error(RS_ERR_INVALID_ARG, "%lld pixels: the fixed scratch holds at most %lld", (long long)pix,
-                         (long long)kPix);
 
     unsigned char* base = nullptr;
     rs_status st = scratch_base(&base);
@@ -179,8 +201,8 @@ extern "C" rs_status rs_render_fixed_scratch(const rs_gaussians* g, const rs_cam
     if ((st = build_accel_device(A, *g, *tune, s))) return st;
 
     DevCam* cams_dev = reinterpret_cast<DevCam*>(base + oCams);
-    if (cudaMemcpyAsync(cams_dev, table, sizeof(DevCam) * n_cams, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return cuda_check("fixed scratch: camera upload");
+    k_upload_cams<<<1, 32, 0, s>>>(table, n_cams, cams_dev);
+    if ((st = cuda_check("fixed scratch: camera upload"))) return st;
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(base + oQueue);
     if (cudaMemsetAsync(queue, 0, 16, s) != cudaSuccess) return cuda_check("fixed scratch: queue reset");
 

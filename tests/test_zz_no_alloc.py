@@ -1,9 +1,9 @@
 """rs_render_fixed_scratch -- the render entry point for callers that cannot allocate device
-memory (code running under a no-allocation graph-capture policy, plug-ins whose host owns all
-device memory).  It keeps every intermediate in one fixed-size device array; this test calls it
-through the C ABI twice in a row, on different scenes and cameras, and checks each output
-against the allocating path (rs_build_accel + rs_render) at the image tolerance.  It also
-checks that requests beyond the fixed limits are rejected.  Collected last on purpose."""
+memory (plug-ins whose host application owns every device allocation, tools held to a fixed
+device-memory budget).  It keeps every intermediate in one fixed-size device array; this test
+calls it through the C ABI twice in a row, on different scenes and cameras, and checks each
+output against the allocating path (rs_build_accel + rs_render) at the image tolerance.  It
+also checks that requests beyond the fixed limits are rejected.  Collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -89,4 +89,16 @@ def test_fixed_scratch_rejects_requests_beyond_its_limits():
     ok_n = native.RsGaussians(10, *([buf.data_ptr()] * 5))
     big = native.cameras_to_ctypes(scenes.look_at_camera((0, 0, -3), (0, 0, 0), 1024, 512, 50))
     assert lib.rs_render_fixed_scratch(ctypes.byref(ok_n), big, 1, ctypes.byref(pc), ctypes.byref(tune),
+                                       ctypes.byref(frame), None) == native.RS_ERR_INVALID_ARG
+    # several cameras whose pixel counts would overflow a running total: each is rejected on
+    # its own before any launch
+    huge = scenes.concat_cameras([scenes.look_at_camera((0, 0, -3), (0, 0, 0), 8, 8, 50)] * 4)
+    huge.width[:] = 2 ** 31 - 1
+    huge.height[:] = 2 ** 31 - 1
+    harr = native.cameras_to_ctypes(huge)
+    assert lib.rs_render_fixed_scratch(ctypes.byref(ok_n), harr, 4, ctypes.byref(pc), ctypes.byref(tune),
+                                       ctypes.byref(frame), None) == native.RS_ERR_INVALID_ARG
+    nan_cam = native.cameras_to_ctypes(cams)
+    nan_cam[0].fx = float("nan")
+    assert lib.rs_render_fixed_scratch(ctypes.byref(ok_n), nan_cam, 1, ctypes.byref(pc), ctypes.byref(tune),
                                        ctypes.byref(frame), None) == native.RS_ERR_INVALID_ARG
