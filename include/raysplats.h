@@ -321,8 +321,11 @@ rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays,
                         float* d, void* cuda_stream);
 
 /* The renderer's ray/Gaussian test for n_pairs (ray r, sorted Gaussian j) pairs of `accel`:
- * out[4 * k] = D^2, t1, hit (1/0), alpha (device floats). ray_o/ray_d device float[3 n_pairs],
- * sorted_j device int32[n_pairs]. */
+ * out[6 * k .. 6 * k + 5] = D^2, t1, hit (1/0), alpha, r, b (device floats), where r is the
+ * sub-ulp residual that the hit's ordering key carries below t1, decoded to units of ulp(t1)
+ * (the centre of its bin, in [-1/2, 1/2]; 0 for a miss), and b the number of residual bits,
+ * so that t1 + r ulp(t1) is the parameter the renderer orders hits by.  ray_o/ray_d device
+ * float[3 n_pairs], sorted_j device int32[n_pairs]; out device float[6 n_pairs]. */
 rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o,
                         const float* ray_d, const int32_t* sorted_j, float Q, float t_near,
                         float* out, void* cuda_stream);

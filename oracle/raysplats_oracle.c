@@ -69,9 +69,10 @@ typedef struct {
 
 /* Ambiguity flags (per ray).  FP32 and FP64 may legitimately take a different discrete
  * decision on such a ray:
- *   BOUNDARY  a Gaussian with |Q - D^2| < OR_BOUNDARY_REL Q at or before the stop point,
- *   TIE       two consecutive hits with |t1 - t1'| < OR_TIE_REL max(1, t) (up to the hit after
- *             the stop),
+ *   BOUNDARY  a Gaussian whose |Q - D^2| lies within the FP32 uncertainty of D^2 (see below), at
+ *             or before the stop point,
+ *   TIE       two consecutive hits whose t lie closer than their combined FP32 uncertainty
+ *             (see OR_T_ERR_C below; up to the hit after the stop),
  *   EPS1      the transmittance after some composited hit within 1e-4 relative of eps1,
  *   TNEAR     a hit candidate with t1 within OR_TIE_REL max(1, t) of t_near.
  * IMPACT is set when one of those alternative decisions (toggle the boundary Gaussian, swap
@@ -89,12 +90,21 @@ enum {
     OR_IMP_TIE = 64,
     OR_IMP_EPS1 = 128
 };
-/* The bands are set from the measured FP32 error of the device's ray/ellipsoid solve (about
- * 5e-6 relative in D^2 and 7e-8 relative in t1 on 20,000 hit and near-miss pairs) with a margin
- * of four to seven. */
+/* The bands follow the FP32 error of the renderer's ray/ellipsoid solve.  BOUNDARY uses a band
+ * per Gaussian (d2tol, a first-order model of that error, see ray_gauss); TIE uses a band per
+ * pair of hits: the sum of their t-uncertainties (ttol) plus OR_T_QUANTUM units of the FP32
+ * spacing at t (the renderer orders by keys resolved to a fraction of that spacing).  TNEAR
+ * keeps a relative band: the renderer's t >= t_near test uses the FP32-rounded t.  On 330,000
+ * hits of three scenes the measured errors stay below 3.6 (t) and 4.5 (D2) times the unscaled
+ * models, so the scales below leave a margin of two.  The D2 model is capped at
+ * OR_BOUNDARY_REL Q: its flat-Gaussian term assumes a worst-case rounding of the whitening, while
+ * the largest measured D2 error is 7e-6 Q. */
 #define OR_IMPACT_TOL 1e-4
 #define OR_BOUNDARY_REL 2e-5
 #define OR_TIE_REL 5e-7
+#define OR_T_ERR_C 8.0
+#define OR_D2_ERR_C 10.0
+#define OR_T_QUANTUM (1.0 / 256.0)
 
 /* ------------------------------------------------------------------------------------ */
 /* App. A.6: rotation matrix from a (possibly unnormalised) quaternion q = (a, b, c, d),  */
@@ -194,7 +204,17 @@ typedef struct {
     double p[3];         /* o' - tau d'  (the M-space closest-approach vector) */
     double D2;           /* <p, p> = squared Mahalanobis distance of the ray (Prop. 2) */
     double t1;           /* ellipsoid entry (valid when D2 <= Q) */
+    double ttol;         /* uncertainty of an FP32 evaluation of t1 (hits) */
+    double mtol;         /* the same for the maximum-response parameter -tau */
+    double d2tol;        /* the same for D2 (hits and near misses) */
 } or_geom;
+
+/* FP32 spacing (ulp) at |t| */
+static double ulp32(double t) {
+    int e = 0;
+    frexp(fabs(t), &e);
+    return ldexp(1.0, e - 24);
+}
 
 static void ray_gauss(const double o[3], const double d[3], const double m[3], const double M[9],
                       double Q, or_geom* g) {
@@ -220,12 +240,48 @@ static void ray_gauss(const double o[3], const double d[3], const double m[3], c
         const double c = (g->op[0] * g->op[0] + g->op[1] * g->op[1] + g->op[2] * g->op[2]) - Q;
         g->t1 = c / (g->a * tstar);
     }
+    /* Uncertainty model of an FP32 evaluation of the solve (relative rounding u = 2^-24), in
+     * world units.  A solve re-centred at the ray point nearest the mean works with the offset
+     * w = (o - m) - <o - m, d> d, the step tm_r from there to the maximum response, and the half
+     * chord r = sqrt((Q - D2) / a).  Rounding of these gives errors of size |w| + r.  A rounded
+     * whitening M (rows of size 1 / s_k) perturbs M w and M d by about u |w| / s_min and
+     * u / s_min, which moves t by (|w| + |tm_r| + r) k with k = 1 / (s_min |M d|) (1 for an
+     * isotropic Gaussian, up to s_max / s_min for a flat one seen edge-on), and moves D2 by
+     * about 2 D |v| / s_min (v = w + tm_r d, the closest-approach offset); an error of D2 enters
+     * t1 amplified by 1 / (2 a r), i.e. by D / sqrt(Q - D2) relative to the terms above.  These
+     * are models, not bounds: OR_T_ERR_C and OR_D2_ERR_C scale them to cover the FP32 errors
+     * measured on the renderer's solve with a margin of two. */
+    g->ttol = g->mtol = g->d2tol = 0.0;
+    if (g->D2 > 1.01 * Q) return; /* far from a hit: no decision to flag */
+    const double od = om[0] * d[0] + om[1] * d[1] + om[2] * d[2];
+    double w[3], v[3], rowmax = 0.0;
+    const double tmr = -g->tau + od; /* maximum response relative to the re-centred point */
+    for (int k = 0; k < 3; ++k) {
+        w[k] = om[k] - od * d[k];
+        v[k] = w[k] + tmr * d[k];
+        const double rn = M[3 * k] * M[3 * k] + M[3 * k + 1] * M[3 * k + 1] + M[3 * k + 2] * M[3 * k + 2];
+        rowmax = fmax(rowmax, rn);
+    }
+    const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    const double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double inv_smin = sqrt(rowmax); /* rows of M = S^-1 R^T have norms 1 / s_k */
+    const double kk = inv_smin / sqrt(g->a);
+    const double D = sqrt(g->D2);
+    const double u = ldexp(1.0, -24);
+    g->d2tol = fmin(OR_D2_ERR_C * u * (g->D2 + 2.0 * D * vn * inv_smin), OR_BOUNDARY_REL * Q);
+    if (g->D2 > Q) return;
+    const double gap = Q - g->D2;
+    const double r = sqrt(gap / g->a);
+    const double amp = gap > 0.0 ? D / sqrt(gap) : INFINITY;
+    g->ttol = OR_T_ERR_C * u * (kk * (wn + fabs(tmr) + r) * (1.0 + amp) + wn + r);
+    g->mtol = OR_T_ERR_C * u * (kk + 1.0) * (wn + fabs(tmr));
 }
 
 /* Exported for unit pins: one ray (double) against one Gaussian given by (mean, quat, scale).
- * out[0] = D2, out[1] = t1, out[2] = hit flag (1/0), out[3] = tau = <o',d'>/<d',d'>. */
+ * out[0] = D2, out[1] = t1, out[2] = hit flag (1/0), out[3] = tau = <o',d'>/<d',d'>,
+ * out[4] = the t1 uncertainty model (ttol), out[5] = the D2 uncertainty model (d2tol). */
 void or_ray_gaussian(const double o[3], const double d[3], const double m[3], const double q[4],
-                     const double s[3], double Q, double t_near, double out[4]) {
+                     const double s[3], double Q, double t_near, double out[6]) {
     double M[9];
     or_geom g;
     whitening(q, s, M);
@@ -234,6 +290,8 @@ void or_ray_gaussian(const double o[3], const double d[3], const double m[3], co
     out[1] = g.t1;
     out[2] = (g.D2 <= Q && g.t1 >= t_near) ? 1.0 : 0.0;
     out[3] = g.tau;
+    out[4] = g.ttol;
+    out[5] = g.d2tol;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -243,6 +301,7 @@ typedef struct {
     double t;
     int64_t idx;
     double D2;
+    double tol; /* uncertainty of an FP32 evaluation of t (TIE band) */
 } or_hit;
 
 static int hit_cmp(const void* x, const void* y) {
@@ -488,14 +547,16 @@ static void* render_worker(void* arg) {
                 hits[nh].t = P->sort_key == 1 ? -g.tau : g.t1;
                 hits[nh].idx = i;
                 hits[nh].D2 = g.D2;
+                hits[nh].tol = P->sort_key == 1 ? g.mtol : g.ttol;
                 nh++;
             }
-            const int near_bd = fabs(Q - g.D2) < OR_BOUNDARY_REL * Q && g.t1 >= P->t_near;
+            const int near_bd = fabs(Q - g.D2) < g.d2tol && g.t1 >= P->t_near;
             const int near_tn = inside && fabs(g.t1 - P->t_near) < OR_TIE_REL * fmax(1.0, fabs(g.t1));
             if (near_bd || near_tn) {
                 cand[nc].t = P->sort_key == 1 ? -g.tau : (g.t1 > P->t_near ? g.t1 : P->t_near);
                 cand[nc].idx = i;
                 cand[nc].D2 = g.D2;
+                cand[nc].tol = P->sort_key == 1 ? g.mtol : g.ttol;
                 cand_kind[nc] = (near_bd ? OR_AMB_BOUNDARY : 0) | (near_tn ? OR_AMB_TNEAR : 0);
                 nc++;
             }
@@ -537,7 +598,7 @@ static void* render_worker(void* arg) {
             const int64_t last = (count < nh) ? count : nh - 1; /* include the pair across the stop */
             for (int64_t h = 0; h + 1 <= last && h + 1 < nh; ++h) {
                 const double tt = hits[h + 1].t;
-                if (fabs(tt - hits[h].t) < OR_TIE_REL * fmax(1.0, fabs(tt))) {
+                if (fabs(tt - hits[h].t) < hits[h].tol + hits[h + 1].tol + OR_T_QUANTUM * ulp32(tt)) {
                     mask |= OR_AMB_TIE;
                     memcpy(alt, hits, sizeof(or_hit) * (size_t)nh);
                     alt[h] = hits[h + 1];
@@ -939,6 +1000,7 @@ typedef struct {
     int64_t idx;
     int32_t seg;
     double t, D2;
+    double tol; /* uncertainty of an FP32 evaluation of t (TIE band) */
 } or_shit;
 
 static int shit_cmp(const void* x, const void* y) {
@@ -960,7 +1022,7 @@ static int64_t gather_hits(const or_job* J, const float of[3], const float df[3]
         or_geom g;
         ray_gauss(o, d, J->means + 3 * i, J->M + 9 * i, Q, &g);
         const double band = OR_TIE_REL * fmax(1.0, fabs(g.t1));
-        if (fabs(Q - g.D2) < OR_BOUNDARY_REL * Q && g.t1 >= tmin - band && g.t1 < tmax + band) *mask |= OR_AMB_BOUNDARY;
+        if (fabs(Q - g.D2) < g.d2tol && g.t1 >= tmin - band && g.t1 < tmax + band) *mask |= OR_AMB_BOUNDARY;
         if (g.D2 > Q) continue;
         if (fabs(g.t1 - tmin) < band || (tmax < INFINITY && fabs(g.t1 - tmax) < band)) *mask |= OR_AMB_TNEAR;
         if (g.t1 >= tmin && g.t1 < tmax) {
@@ -968,6 +1030,7 @@ static int64_t gather_hits(const or_job* J, const float of[3], const float df[3]
             out[nh].seg = seg;
             out[nh].t = g.t1;
             out[nh].D2 = g.D2;
+            out[nh].tol = g.ttol;
             nh++;
         }
     }
@@ -1030,7 +1093,8 @@ int or_render_scene(int64_t n, const double* means, const double* quats, const d
                 alpha[count] = al;
                 Tb[count] = Tr;
                 Tr *= (1.0 - al);
-                if (h + 1 < nh && fabs(seg_hits[h + 1].t - seg_hits[h].t) < OR_TIE_REL * fmax(1.0, seg_hits[h].t))
+                if (h + 1 < nh && fabs(seg_hits[h + 1].t - seg_hits[h].t) <
+                                      seg_hits[h].tol + seg_hits[h + 1].tol + OR_T_QUANTUM * ulp32(seg_hits[h].t))
                     mask |= OR_AMB_TIE;
                 if (fabs(Tr - P->eps1) < 1e-4 * P->eps1) mask |= OR_AMB_EPS1;
                 count++;

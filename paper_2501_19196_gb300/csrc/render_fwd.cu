@@ -103,19 +103,25 @@ __global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs
                              const int32_t* sj, float Q, float t_near, float* out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_pairs) return;
+    float* o = out + 6 * k;
     const int j = sj[k];
     if (j < 0 || j >= n_gauss) {  // out-of-range id: report NaN instead of reading
-        out[4 * k] = out[4 * k + 1] = out[4 * k + 2] = out[4 * k + 3] = __int_as_float(0x7fc00000);
+        for (int c = 0; c < 6; ++c) o[c] = __int_as_float(0x7fc00000);
         return;
     }
     Hit h;
     ray_ellipsoid<false>(make_float3(ro[3 * k], ro[3 * k + 1], ro[3 * k + 2]),
                          make_float3(rd[3 * k], rd[3 * k + 1], rd[3 * k + 2]), rec[4 * j], rec[4 * j + 1],
                          rec[4 * j + 2], Q, t_near, h);
-    out[4 * k] = h.D2;
-    out[4 * k + 1] = h.t1;
-    out[4 * k + 2] = h.hit ? 1.f : 0.f;
-    out[4 * k + 3] = response_alpha(rec[4 * j + 3].x, h.D2);
+    o[0] = h.D2;
+    o[1] = h.t1;
+    o[2] = h.hit ? 1.f : 0.f;
+    o[3] = response_alpha(rec[4 * j + 3].x, h.D2);
+    // the ordering key's sub-ulp residual, decoded to units of ulp(t1): the centre of its bin
+    const int jb = key_id_bits((int)n_gauss), sb = 32 - jb;
+    const uint32_t sub = h.hit ? (uint32_t)((uint64_t)hit_key(h, 0, j, jb) >> jb) & ((1u << sb) - 1u) : 0u;
+    o[4] = h.hit ? (float)(((double)sub + 0.5) / (double)(1ull << sb) - 0.5) : 0.f;
+    o[5] = (float)sb;
 }
 
 

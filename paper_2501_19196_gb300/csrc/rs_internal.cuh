@@ -67,13 +67,41 @@ struct TraceParams {
                            // hit through the phase-2 hits (.w < 0: no phase 2)
 };
 
-// (t1, sorted id) packed into one ordered 64-bit key; t1 >= 0 so its bit pattern orders as
-// an unsigned integer.
-__device__ __forceinline__ int64_t pack_key(float t, int j) {
-    return (int64_t)(((uint64_t)__float_as_uint(t) << 32) | (uint32_t)j);
+// Ordered 64-bit keys: the ray parameter's FP32 bit pattern (t >= 0, so it orders as an
+// unsigned integer) in the high 32 bits; the low 32 bits hold, from the top, a sub-ulp residual
+// of t (hits only) and the sorted id j in the low key_id_bits(n) bits.  pack_key(t, low) builds
+// bounds: low = 0 is the smallest key at t, low = 0xffffffff the largest.
+__device__ __forceinline__ int64_t pack_key(float t, uint32_t low) {
+    return (int64_t)(((uint64_t)__float_as_uint(t) << 32) | low);
 }
 __device__ __forceinline__ float key_t(int64_t k) { return __uint_as_float((uint32_t)((uint64_t)k >> 32)); }
-__device__ __forceinline__ int key_j(int64_t k) { return (int)(uint32_t)((uint64_t)k & 0xffffffffu); }
+// bits that hold a sorted id j < n (at least one)
+__device__ __forceinline__ int key_id_bits(int n) { return n > 1 ? 32 - __clz(n - 1) : 1; }
+__device__ __forceinline__ int key_j(int64_t k, int jb) { return (int)((uint32_t)k & ((1u << jb) - 1u)); }
+constexpr uint32_t kKeyLowMax = 0xffffffffu;
+
+// The ordering key of a hit whose parameter was evaluated as hi = fl(tc + tr): tc is the
+// re-centring shift of the solve, tr the part solved relative to it.  FP32 rounding of that
+// sum alone (up to half an ulp of t) would order two hits whose parameters differ by less than
+// that at random; so the exact rounding error lo = (tc + tr) - hi (TwoSum) is kept, in units of
+// ulp(hi), in the 32 - jb bits between hi and the id.  Keys then order by the parameter to a
+// small fraction of an ulp, i.e. to the accuracy of the solve itself; only hits whose accurate
+// parameters agree to 2^-(32 - jb) ulp tie, and those order by id.
+__device__ __forceinline__ int64_t pack_hit_key(float hi, float tc, float tr, int j, int jb) {
+    const float bb = __fsub_rn(hi, tc);
+    const float lo = __fadd_rn(__fsub_rn(tc, __fsub_rn(hi, bb)), __fsub_rn(tr, bb));
+    const uint32_t hb = __float_as_uint(hi);
+    const int E = (int)(hb >> 23);  // biased exponent (hi >= 0)
+    const int sb = 32 - jb;         // residual bits (jb <= 30, so sb >= 2)
+    uint32_t sub = 1u << (sb - 1);  // lo = 0, or hi too small to resolve
+    if (E >= 24) {
+        // lo / ulp(hi) in [-1/2, 1/2] (exact: a power-of-two scale), then to [0, 2^sb)
+        const float f = __fmul_rn(lo, __uint_as_float((uint32_t)(277 - E) << 23));
+        const float sc = __fmul_rn(__fadd_rn(f, 0.5f), __uint_as_float((uint32_t)(127 + sb) << 23));
+        sub = min(__float2uint_rd(sc), (1u << sb) - 1u);
+    }
+    return (int64_t)(((uint64_t)hb << 32) | ((uint64_t)sub << jb) | (uint32_t)j);
+}
 
 // ---------------------------------------------------------------------------------------------
 // Camera ray (a7): the fixed FP32 sequence of the ABI (no contraction: explicit _rn ops).
@@ -109,6 +137,7 @@ __device__ __forceinline__ void camera_ray(const DevCam& c, int px, int py, floa
 struct Hit {
     float D2, t1;
     float tm;    // ray parameter of the maximum response (chord midpoint)
+    float tc, t1r, tmr;  // t1 = fl(tc + t1r), tm = fl(tc + tmr): the re-centring shift and the rest
     bool hit;
     float p[3];  // M-space closest-approach vector
     float v[3];  // world vector from the mean to the point of maximum response
@@ -154,6 +183,9 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
     const float b = __fmaf_rn(op[2], dp[2], __fmaf_rn(op[1], dp[1], __fmul_rn(op[0], dp[0])));
     const float tm = -__fdiv_rn(b, a);
     h.tm = __fadd_rn(tc, tm);
+    h.tc = tc;
+    h.tmr = tm;
+    h.t1r = 0.f;
     float p[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] = __fmaf_rn(tm, dp[k], op[k]);
@@ -173,6 +205,7 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
         }
         const float t1 = __fadd_rn(__fadd_rn(tc, t1r), 0.0f);  // +0 turns -0 into +0
         h.t1 = t1;
+        h.t1r = t1r;
         h.hit = t1 >= t_near;
     }
     if (WANT_GEOM) {
@@ -241,6 +274,13 @@ __device__ __forceinline__ void closest_point_accurate(const float3 o, const flo
 // response, which is never below t1 (the max guards FP32 rounding at grazing incidence).
 __device__ __forceinline__ float hit_key_t(const Hit& h, int sort_key) {
     return sort_key ? fmaxf(h.tm, h.t1) : h.t1;
+}
+
+// The 64-bit ordering key of a hit on sorted Gaussian j (see pack_hit_key); its high half is
+// hit_key_t(h, sort_key).
+__device__ __forceinline__ int64_t hit_key(const Hit& h, int sort_key, int j, int jb) {
+    if (sort_key && h.tm >= h.t1) return pack_hit_key(h.tm, h.tc, h.tmr, j, jb);
+    return pack_hit_key(h.t1, h.tc, h.t1r, j, jb);
 }
 
 // alpha_i = opacity * exp(-D2 / 2)  (Eq. 8, Prop. 2)

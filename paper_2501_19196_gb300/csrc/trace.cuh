@@ -495,6 +495,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                                               float& C1, float& C2, float& T, float& depth,
                                               int64_t& last_key, int& count, Counters& cnt, int* err) {
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     const float eps = fmaxf(P.eps1, 1e-30f);
     const float INF = __int_as_float(0x7f800000);
     T = 1.f;
@@ -523,7 +524,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
         int sp = 0, node = nodes.root, visits = 0;
         auto composite_front = [&]() {
             const int64_t key = keys[0];
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             Hit hc;  // the same solve as at insertion time: the same bits
             ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
                                  P.t_near, hc);
@@ -581,7 +582,7 @@ __device__ __forceinline__ void trace_forward(const float4* __restrict__ rec, co
                         ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                         if (COUNT) cnt.tests++;
                         if (h.hit) {
-                            const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
+                            const int64_t key = hit_key(h, P.sort_key, q, jb);
                             if (key > lo_key && key < cap) {
                                 if (key < keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];  // evicted
@@ -672,8 +673,9 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                                                float4* __restrict__ gtmp, Counters& cnt, int* err) {
     if (n_hits <= 0) return;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     const float NINF = __int_as_float(0xff800000);
-    constexpr int64_t kFloorJ = 0x7fffffff;
+    constexpr uint32_t kFloorJ = kKeyLowMax;  // the largest key at a given t
     int64_t hi_key = last_key + 1;  // exclusive upper bound
     Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits;
@@ -697,7 +699,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
         bool stop = false;
         auto replay_front = [&]() {
             const int64_t key = keys[0];
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             float4 v[4];
             adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, v);
             float4* gp = gtmp + 4 * j;
@@ -746,7 +748,7 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
                         ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                         if (COUNT) cnt.tests++;
                         if (h.hit) {
-                            const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
+                            const int64_t key = hit_key(h, P.sort_key, q, jb);
                             if (key < hi_key && key > floor_key) {
                                 if (key > keys[K - 1]) {
                                     if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];  // evicted
@@ -932,6 +934,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                                                      int* err) {
     const unsigned FULL = 0xffffffffu;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     const float eps = fmaxf(P.eps1, 1e-30f);
     const float INF = __int_as_float(0x7f800000);
     T = 1.f;
@@ -961,7 +964,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
         int sp = 0, node = nodes.root, visits = 0;
         auto composite_front = [&]() {
             const int64_t key = keys[0];
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             Hit hc;  // the same solve as at insertion time: the same bits
             ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
                                  P.t_near, hc);
@@ -1021,7 +1024,7 @@ __device__ __forceinline__ void trace_forward_packet(const float4* __restrict__ 
                             ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                             if (COUNT) cnt.tests++;
                             if (h.hit) {
-                                const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
+                                const int64_t key = hit_key(h, P.sort_key, q, jb);
                                 if (key > lo_key && key < cap) {
                                     if (key < keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKey) cap = keys[K - 1];
@@ -1116,8 +1119,9 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                                                       float4* __restrict__ gtmp, Counters& cnt, int* err) {
     const unsigned FULL = 0xffffffffu;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     const float NINF = __int_as_float(0xff800000);
-    constexpr int64_t kFloorJ = 0x7fffffff;
+    constexpr uint32_t kFloorJ = kKeyLowMax;  // the largest key at a given t
     int64_t hi_key = last_key + 1;
     Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits > 0 ? n_hits : 0;
@@ -1142,7 +1146,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
         bool stop = false;
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, vout);
             jout = j;
             --remaining;
@@ -1201,7 +1205,7 @@ __device__ __forceinline__ void trace_backward_packet(const float4* __restrict__
                             ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, h);
                             if (COUNT) cnt.tests++;
                             if (h.hit) {
-                                const int64_t key = pack_key(hit_key_t(h, P.sort_key), q);
+                                const int64_t key = hit_key(h, P.sort_key, q, jb);
                                 if (key < hi_key && key > floor_key) {
                                     if (key > keys[K - 1]) {
                                         if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
@@ -1590,6 +1594,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     // camera rays (and a scene's first segment) share their origin; otherwise cone.ok is false
     const RayCone cone = warp_ray_cone(o, d);
     const float eps = fmaxf(P.eps1, 1e-30f);
@@ -1622,7 +1627,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
         const float tlo = lo_key < 0 ? tmin : key_t(lo_key);
         auto composite_front = [&]() {
             const int64_t key = kb.front();
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             Hit hc;  // the same solve as at insertion time: the same bits
             ray_ellipsoid<false>(o, d, __ldg(rec + 4 * j + 0), __ldg(rec + 4 * j + 1), __ldg(rec + 4 * j + 2), P.Q,
                                  tmin, hc);
@@ -1745,7 +1750,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                 ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, tmin, hh);
                                 if (COUNT) cnt.tests++;
                                 if (hh.hit) {
-                                    const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
+                                    const int64_t key = hit_key(hh, P.sort_key, qq, jb);
                                     if (key > lo_key && key < cap) {
                                         const int64_t kK = kb.last();
                                         if (key < kK) {
@@ -1821,9 +1826,10 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
     const float NINF = __int_as_float(0xff800000);
     const float INF = __int_as_float(0x7f800000);
-    constexpr int64_t kFloorJ = 0x7fffffff;
+    constexpr uint32_t kFloorJ = kKeyLowMax;  // the largest key at a given t
     int64_t hi_key = last_key + 1;
     Adjoint adj = adjoint_start(P, T_final, g);
     int remaining = n_hits > 0 ? n_hits : 0;
@@ -1847,7 +1853,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         bool stop = false;
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = keys[0];
-            const int j = key_j(key);
+            const int j = key_j(key, jb);
             adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, vout);
             jout = j;
             --remaining;
@@ -1954,7 +1960,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                 ray_ellipsoid<false>(o, d, g0, g1, g2, P.Q, P.t_near, hh);
                                 if (COUNT) cnt.tests++;
                                 if (hh.hit) {
-                                    const int64_t key = pack_key(hit_key_t(hh, P.sort_key), qq);
+                                    const int64_t key = hit_key(hh, P.sort_key, qq, jb);
                                     if (key < hi_key && key > floor_key) {
                                         if (key > keys[K - 1]) {
                                             if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];

@@ -48,7 +48,13 @@ def oracle_pixels(scene, cams, cam, px, py, prm, dl_rgb=None, dl_alpha=None, dl_
                          eps2=prm.eps2)
 
 
-def compare_image(gpu, ora, idx, tol=TOL_RGB, max_masked=0.02, label=""):
+# Largest fraction of pixels that the oracle may exclude from parity (IMPACT flag: an FP32
+# decision that FP64 could take the other way changes the pixel by more than 1e-4).  The
+# workloads' samples stay at or below it; tests with a different figure state why.
+MAX_MASKED = 0.001
+
+
+def compare_image(gpu, ora, idx, tol=TOL_RGB, max_masked=MAX_MASKED, label=""):
     """Element-wise parity on pixels whose value is unique at the tolerance (oracle's IMPACT
     flag clear).  Returns (max rgb/alpha error, masked fraction)."""
     ok = (ora["mask"] & oracle.AMB_IMPACT) == 0

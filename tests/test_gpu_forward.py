@@ -132,24 +132,39 @@ def test_hit_test_numerics_against_fp64():
     d = (target - o).astype(np.float64)
     d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
     out = r.debug_hits(torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda(),
-                       torch.from_numpy(j.astype(np.int32)).cuda(), Q).cpu().numpy()
+                       torch.from_numpy(j.astype(np.int32)).cuda(), Q).cpu().numpy().astype(np.float64)
     r.close()
     D2 = np.zeros(k)
     t1 = np.zeros(k)
+    tol = np.zeros(k)
+    d2tol = np.zeros(k)
     hit = np.zeros(k, bool)
     for t in range(k):
-        D2[t], t1[t], hit[t], _ = oracle.ray_gaussian(o[t], d[t], sc.means[gi[t]], sc.quats[gi[t]],
-                                                      sc.scales[gi[t]], Q)
-    clear = np.abs(D2 - Q) > 2e-5 * Q   # the oracle's boundary band
+        D2[t], t1[t], hit[t], _, tol[t], d2tol[t] = oracle.ray_gaussian(o[t], d[t], sc.means[gi[t]], sc.quats[gi[t]],
+                                                                        sc.scales[gi[t]], Q, with_tol=True)
+    near = D2 <= Q * (1.0 + 1e-3)  # pairs whose D2 decides a hit
+    ratio_d2 = np.abs(out[near, 0] - D2[near]) / d2tol[near]
+    clear = np.abs(D2 - Q) >= d2tol   # outside the oracle's boundary band
     assert np.mean(hit) > 0.2
     assert np.all((out[clear, 2] > 0.5) == hit[clear])
     both = clear & hit
     errD = np.abs(out[both, 0] - D2[both]) / np.maximum(1.0, D2[both])
     errt = np.abs(out[both, 1] - t1[both]) / np.maximum(1.0, np.abs(t1[both]))
-    print(f"hit numerics: max |dD2|/max(1,D2) = {errD.max():.3e}, max |dt1|/max(1,t1) = {errt.max():.3e}")
-    # the oracle's ambiguity bands (2e-5 Q in D2, 5e-7 in t1) assume these bounds with margin
+    # the ordering parameter: t1 plus the key's sub-ulp residual
+    ulp = np.ldexp(1.0, np.frexp(out[both, 1])[1] - 24)
+    t_key = out[both, 1] + out[both, 4] * ulp
+    quantum = ulp * np.ldexp(1.0, -out[both, 5].astype(np.int64))
+    err_key = np.abs(t_key - t1[both])
+    ratio = err_key / (tol[both] + 0.5 * quantum)
+    print(f"hit numerics: max |dD2|/max(1,D2) = {errD.max():.3e}, max |dt1|/max(1,t1) = {errt.max():.3e}; "
+          f"ordering key: max error {np.max(err_key / ulp):.3e} ulp (median {np.median(err_key / ulp):.2e}), "
+          f"max error / oracle band {ratio.max():.3f} (99.9% {np.quantile(ratio, 0.999):.3f}); "
+          f"D2: max error / oracle band {ratio_d2.max():.3f} (99.9% {np.quantile(ratio_d2, 0.999):.3f})")
     assert errD.max() < 1e-5
     assert errt.max() < 2.5e-7
+    # the oracle's per-hit TIE and BOUNDARY bands cover the errors with a margin of two
+    assert ratio.max() < 0.5
+    assert ratio_d2.max() < 0.5
 
 
 # ------------------------------------------------------------------------------------------
@@ -183,14 +198,15 @@ def test_forward_random_tiny_scenes(seed, case):
     g = gpu_render(sc, cams, prm)
     cam, px, py = scenes.pixel_grid(cams)
     ora = oracle_pixels(sc, cams, cam, px, py, prm)
-    compare_image(g, ora, pixel_index(cams, cam, px, py), max_masked=0.03, label=f"seed {seed} {kw}")
+    # 503 pixels: one masked pixel is 0.2 %; at most two (measured: at most one)
+    compare_image(g, ora, pixel_index(cams, cam, px, py), max_masked=0.004, label=f"seed {seed} {kw}")
 
 
 def test_forward_shell_200k_sampled_and_crop():
     wl = scenes.workload(2)
     prm = params(eps1=wl.eps1, background=wl.background)
     g = gpu_render(wl.scene, wl.cams, prm)
-    cam, px, py = scenes.pixel_grid(wl.cams, stride=29)
+    cam, px, py = scenes.pixel_grid(wl.cams, stride=20)
     ora = oracle_pixels(wl.scene, wl.cams, cam, px, py, prm)
     err, masked = compare_image(g, ora, pixel_index(wl.cams, cam, px, py), label="200k sampled")
     print(f"200k/800x800 sampled: max err {err:.2e}, masked {masked:.4f}, pixels {len(cam)}")
@@ -201,16 +217,20 @@ def test_forward_shell_200k_sampled_and_crop():
     g2 = gpu_render(wl.scene, crop, prm)
     cam, px, py = scenes.pixel_grid(crop)
     ora = oracle_pixels(wl.scene, crop, cam, px, py, prm)
-    compare_image(g2, ora, pixel_index(crop, cam, px, py), label="200k crop")
+    # the crop looks through both walls of the shell near its centre (about twice the hits of an
+    # average ray, spaced about 2e-3 apart): 4 of its 1,920 rays (0.21 %) hold a pair of hits
+    # closer than their FP32 uncertainty whose swap changes the colour by more than 1e-4
+    compare_image(g2, ora, pixel_index(crop, cam, px, py), max_masked=0.003, label="200k crop")
 
 
 def test_forward_unbounded_1m_sampled():
     wl = scenes.workload(3)
     prm = params(eps1=wl.eps1, background=wl.background)
     g = gpu_render(wl.scene, wl.cams, prm)
-    cam, px, py = scenes.pixel_grid(wl.cams, stride=53)
+    cam, px, py = scenes.pixel_grid(wl.cams, stride=33)
     ora = oracle_pixels(wl.scene, wl.cams, cam, px, py, prm)
-    err, masked = compare_image(g, ora, pixel_index(wl.cams, cam, px, py), label="1M sampled")
+    # 1,014 pixels: one masked pixel is 0.1 % (measured: one, a D2 within FP32 error of Q)
+    err, masked = compare_image(g, ora, pixel_index(wl.cams, cam, px, py), max_masked=0.002, label="1M sampled")
     print(f"1M/1280x832 sampled: max err {err:.2e}, masked {masked:.4f}, pixels {len(cam)}")
 
 
@@ -330,6 +350,10 @@ def test_rays_starting_inside_many_overlapping_boxes():
     cam, px, py = scenes.pixel_grid(cams)
     ora = oracle_pixels(sc, cams, cam, px, py, prm)
     assert np.median(ora["n_hits"]) > 200  # several passes of K = 32 per ray
+    # Large Gaussians (scale about 0.35) next to the camera: the FP32 error of a hit's t grows
+    # with the Gaussian's size (up to 2e-6 here, against spacings of about 1e-2 between the ~200
+    # hits of a ray), so about 2 % of these rays hold a pair of hits whose order FP32 cannot
+    # decide and whose swap changes the colour by more than 1e-4 (the oracle's per-hit TIE band).
     for tune in (dict(), dict(traversal=1), dict(kbuf=8)):
         g = gpu_render(sc, cams, prm, tune=native.default_tune(**tune))  # raises on a loop-guard error
-        compare_image(g, ora, pixel_index(cams, cam, px, py), label=f"dense overlap {tune}")
+        compare_image(g, ora, pixel_index(cams, cam, px, py), max_masked=0.03, label=f"dense overlap {tune}")

@@ -100,7 +100,9 @@ def test_image_matches_the_scene_oracle(seed):
     e_d = (np.abs(g["depth"][idx][ok] - ora["depth"][ok]) / np.maximum(1.0, ora["depth"][ok])).max()
     print(f"[parity] scene seed {seed}: rays {len(ok)} masked {1 - ok.mean():.4f} max|d rgb| {e_rgb:.2e} "
           f"max|d alpha| {e_a:.2e} depth rel {e_d:.2e}")
-    assert ok.mean() > 0.95
+    # the scene oracle masks every ray with an FP32-sensitive decision (surface edges and ties,
+    # Gaussian boundaries and ties, eps1), without testing its impact: measured at most 0.11 %
+    assert ok.mean() >= 0.997
     assert e_rgb <= TOL_RGB and e_a <= TOL_RGB and e_d <= 1e-3
 
 
@@ -169,6 +171,7 @@ def test_mirror_workload_full_size_sampled():
     errs = {k: rel_l2(grads[k].reshape(ora["grads"][k].shape), ora["grads"][k]) for k in KEYS}
     print(f"[parity] mirror workload sampled: pixels {len(cam)} masked {1 - ok.mean():.4f} max|d rgb| {e_rgb:.2e} "
           f"max|d alpha| {e_a:.2e}", {k: f"{v:.2e}" for k, v in errs.items()})
-    assert ok.mean() > 0.95
+    # every flagged decision masks (no impact test); 117 rays, one of them masked (0.85 %)
+    assert (~ok).sum() <= 2
     assert e_rgb <= TOL_RGB and e_a <= TOL_RGB
     assert max(errs.values()) < TOL_GRAD, errs
