@@ -35,8 +35,11 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one capture,
 # profiles/k_render_dram_traffic_1m_gaussians_16cams.md): the forward kernel, and the hit-list
 # replay for the adjoint.  Reported only while the kernel sources are unchanged (hash).
-KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu")
+KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
 TRAFFIC = {"kernels": "b4d0d7e12cc0a33d", "fwd_bytes": 6.16e9, "bwd_bytes": 5.25e9}
+# fraction of cycles with an instruction issued (smsp__issue_active.avg.pct_of_peak_sustained_active)
+# of the forward and the list replay, from the small-case --set full profile of the same sources
+ISSUE_ACTIVE = {"kernels": "", "fwd": None, "bwd": None}
 
 
 def parse():
@@ -63,6 +66,8 @@ def parse():
     p.add_argument("--traversal", type=int, default=None)
     p.add_argument("--hit-list", type=int, default=None, help="per-ray hit-list capacity (0: adjoint re-traverses)")
     p.add_argument("--smem-nodes", type=int, default=None)
+    p.add_argument("--no-autotune", action="store_true", help="default tunables instead of the autotuner's pick")
+    p.add_argument("--no-parity", action="store_true", help="skip the oracle check of the bench's own outputs")
     p.add_argument("--profile", action="store_true",
                    help="ncu mode: `warmup` eager batched steps, then one more step, then exit (no JSON)")
     return p.parse_args()
@@ -165,6 +170,89 @@ def make_workload(args):
                                       scenes.look_at_camera((0.0, 2.0, 12.0), (0, 0, 0), 640, 416, 60.0)])
         wl = scenes.Workload(wl.name + "_small2cams", wl.scene, cams, wl.Q, wl.eps1, wl.k_max, wl.background, True)
     return wl
+
+
+def bench_config(wl, world=1):
+    """The workload description both arms print (identical, so the two lines compare)."""
+    return {"workload": wl.name, "gaussians": int(wl.scene.n), "cameras": int(wl.cams.count),
+            "rays_per_step": int(wl.cams.total_rays()),
+            "step": "LBVH rebuild + forward render + adjoint, all cameras",
+            "l2": "flushed between timed steps (256 MiB write, untimed)", "parallelism": f"replicas x{world}"}
+
+
+def step_stats(ms_list):
+    """Mean (the contract's time per step), median, min and max of the timed steps (ms)."""
+    return {"mean": sum(ms_list) / len(ms_list), "median": statistics.median(ms_list), "min": min(ms_list),
+            "max": max(ms_list)}
+
+
+def parity_pixels(cams, target=1000):
+    """A fixed stratified sample of about `target` distinct pixels: every s-th pixel in x and y
+    of every camera."""
+    import numpy as np
+    from workloads import scenes
+    s = max(1, int(round((cams.total_rays() / target) ** 0.5)))
+    cam, px, py = scenes.pixel_grid(cams, stride=s)
+    base = np.concatenate([[0], np.cumsum(cams.n_pixels())[:-1]])
+    idx = base[cam] + py.astype(np.int64) * cams.width[cam].astype(np.int64) + px
+    return cam, px, py, idx, s
+
+
+def bench_parity(wl, prm, replay, outs, grads, d_rgb, d_alpha, target=1000, seed=11):
+    """The oracle against the benchmark's own outputs: the captured step (`replay`) runs once
+    more with an upstream gradient on a stratified pixel sample only (zero elsewhere, and zero
+    on rays whose discrete decisions FP32 may take differently), then its image at those pixels
+    and its gradients are compared with the FP64 oracle's."""
+    import numpy as np
+    import torch
+    import oracle
+    cam, px, py, idx, stride = parity_pixels(wl.cams, target)
+    sc = wl.scene
+    ora0 = oracle.render(sc, wl.cams, cam, px, py, prm.Q, prm.eps1, prm.k_max, prm.background)
+    bad = (ora0["mask"] & oracle.AMB_DECISION) != 0
+    rng = np.random.default_rng(seed)
+    gc = rng.standard_normal((len(cam), 3))
+    ga = rng.standard_normal(len(cam))
+    gc[bad] = 0.0
+    ga[bad] = 0.0
+    ora = oracle.render(sc, wl.cams, cam, px, py, prm.Q, prm.eps1, prm.k_max, prm.background, dl_rgb=gc, dl_alpha=ga)
+    keep = (d_rgb.clone(), d_alpha.clone())
+    ti = torch.from_numpy(idx).to(d_rgb.device)
+    d_rgb.zero_()
+    d_alpha.zero_()
+    d_rgb[ti] = torch.from_numpy(gc.astype(np.float32)).to(d_rgb.device)
+    d_alpha[ti] = torch.from_numpy(ga.astype(np.float32)).to(d_rgb.device)
+    replay()
+    torch.cuda.synchronize()
+    rgb = outs[0][ti].cpu().numpy().astype(np.float64)
+    alpha = outs[1][ti].cpu().numpy().astype(np.float64)
+    depth = outs[2][ti].cpu().numpy().astype(np.float64)
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}
+    d_rgb.copy_(keep[0])
+    d_alpha.copy_(keep[1])
+    ok = (ora["mask"] & oracle.AMB_IMPACT) == 0
+    e_rgb = float(np.abs(rgb[ok] - ora["rgb"][ok]).max(initial=0.0))
+    e_a = float(np.abs(alpha[ok] - ora["alpha"][ok]).max(initial=0.0))
+    e_d = float((np.abs(depth[ok] - ora["depth"][ok]) / np.maximum(1.0, ora["depth"][ok])).max(initial=0.0))
+    rel = {}
+    for k in ("means", "quats", "scales", "opacities", "rgb"):
+        ref = ora["grads"][k]
+        rel[k] = float(np.linalg.norm(got[k].reshape(ref.shape) - ref) / max(np.linalg.norm(ref), 1e-30))
+    ok_all = e_rgb <= 2e-4 and e_a <= 2e-4 and max(rel.values()) <= 1e-3
+    return {"pixels": int(len(cam)), "sample": f"every {stride}th pixel in x and y of every camera",
+            "masked_frac": float(1.0 - ok.mean()), "decision_flagged_frac": float(bad.mean()),
+            "max_abs_rgb": e_rgb, "max_abs_alpha": e_a, "max_rel_depth": e_d, "grad_rel_l2": rel,
+            "tolerance": {"rgb_alpha_abs": 2e-4, "grad_rel_l2": 1e-3}, "pass": bool(ok_all),
+            "path": "the timed CUDA graph, replayed with the sampled upstream gradient"}
+
+
+def bench_candidates(native, base):
+    """The autotuner's candidates for the benchmark: the default and three neighbours."""
+    d = base.as_dict()
+    out = [native.default_tune(**d)]
+    for kw in (dict(tile_w=4, tile_h=8), dict(leaf_size=24), dict(morton_bits=20)):
+        out.append(native.default_tune(**dict(d, **kw)))
+    return out
 
 
 def _timed_events(fn, steps, warmup, flush, stream):
@@ -289,8 +377,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "gaussians": wl.scene.n, "cameras": wl.cams.count,
-                   "rays_per_step": int(wl.cams.total_rays()), "path": "FP64 CPU oracle (brute force)"},
+        "config": bench_config(wl, 1), "path": "FP64 CPU oracle (brute force)",
         "cpu_baseline": {"value": value, "unit": "Mrays/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -348,8 +435,21 @@ def run_ours(args):
         overrides["smem_nodes"] = args.smem_nodes
     if args.hit_list is not None:
         overrides["hit_list"] = args.hit_list
-    tune_b = native.default_tune(persistent=1, **overrides)
-    tune_p = native.default_tune(persistent=0, **overrides)
+    tune_default = native.default_tune(persistent=1, **overrides)
+    autotune = None
+    tune_b = tune_default
+    if not overrides and not args.no_autotune and not args.profile:
+        # the batched arm runs the autotuner's pick (cached per GPU / scene size / rays / cameras)
+        from paper_2501_19196_gb300 import tune as tuner
+        cands = bench_candidates(native, tune_default)
+        t0 = time.perf_counter()
+        tune_b, table = tuner.autotune(params, wl.cams, prm, d_rgb=d_rgb, d_alpha=d_alpha, cands=cands, reps=3)
+        autotune = {"chosen": tune_b.as_dict(), "candidates": len(cands), "seconds": time.perf_counter() - t0,
+                    "ms_per_candidate": {json.dumps(c.as_dict(), sort_keys=True): table.get(
+                        json.dumps(c.as_dict(), sort_keys=True)) for c in cands},
+                    "default_ms": table.get(json.dumps(tune_default.as_dict(), sort_keys=True)),
+                    "timing": "rs_tune: eager LBVH rebuild + forward + adjoint, CUDA events, 3 repetitions"}
+    tune_p = native.default_tune(**dict(tune_b.as_dict(), persistent=0))
     n = wl.scene.n
     outs = (torch.empty((P, 3), device=dev), torch.empty(P, device=dev), torch.empty(P, device=dev))
     grads = {"means": torch.zeros((n, 3), device=dev), "quats": torch.zeros((n, 4), device=dev),
@@ -376,7 +476,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(fn, steps, warmup, sampler=None):
+    step_ms = {}
+
+    def timed(fn, steps, warmup, sampler=None, name=None):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
@@ -394,7 +496,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / steps, world, dev)
+        each = [a.elapsed_time(b) for a, b in evs]
+        if name:
+            step_ms[name] = step_stats(each)
+        ms = max_over_ranks(sum(each) / steps, world, dev)
         return ms, clocks
 
     if args.profile:
@@ -430,9 +535,16 @@ def run_ours(args):
     g_f = capture(lambda: step(rb, False))
 
     sampler = ClockSampler(local)
-    ms_fb, clocks = timed(g_fb.replay, args.steps, args.warmup, sampler)
-    ms_f, _ = timed(g_f.replay, args.steps, args.warmup)
+    ms_fb, clocks = timed(g_fb.replay, args.steps, args.warmup, sampler, name="fwd_bwd")
+    ms_f, _ = timed(g_f.replay, args.steps, args.warmup, name="fwd")
     rb.check_device()
+    # the oracle against this run's own outputs (the same graph, replayed once more)
+    parity = None
+    if rank == 0 and not args.no_parity:
+        t0 = time.perf_counter()
+        parity = bench_parity(wl, prm, g_fb.replay, outs, grads, d_rgb, d_alpha)
+        parity["seconds"] = time.perf_counter() - t0
+        rb.check_device()
     ms_fb_nograph, _ = timed(lambda: step(rb, True), max(3, args.steps // 2), 1)
     # the adjoint without hit lists (every ray re-traverses the BVH), same graph-captured step
     replay = None
@@ -506,8 +618,17 @@ def run_ours(args):
     traffic = None
     if TRAFFIC.get("kernels") == src_hash():
         traffic = TRAFFIC["bwd_bytes" if dom == "bwd" else "fwd_bytes"]
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": traffic, "kernel": "adjoint: k_replay_list + k_render_bwd + k_finalize" if dom == "bwd"
+    # The dominant kernel is bound by instruction issue and latency (small-case --set full
+    # profile: issue slots busy ISSUE_ACTIVE of the time, DRAM nearly idle), not by HBM: `frac`
+    # is the touched-bytes fraction (node, record and output bytes the method must read, mostly
+    # L1/L2 hits) against the HBM copy peak, and `dram_frac` the measured DRAM traffic's.
+    roofline = {"bound": "issue/latency", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "frac_kind": "touched (algorithmic) bytes over the HBM copy peak",
+                "traffic": traffic,
+                "dram_frac": (traffic / (kms[dom] * 1e-3) / 1e9 / hbm) if traffic else None,
+                "issue_active": ISSUE_ACTIVE.get("fwd" if dom == "fwd" else "bwd")
+                if ISSUE_ACTIVE.get("kernels") == src_hash() else None,
+                "kernel": "adjoint: k_replay_list + k_render_bwd + k_finalize" if dom == "bwd"
                 else "k_render_fwd (persistent)", "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": dom_bytes, "kernel_ms": kms[dom],
                 "counts_fwd": sf, "counts_bwd": sb,
@@ -613,12 +734,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "gaussians": n, "cameras": wl.cams.count, "rays_per_step": P,
-                   "step": "LBVH rebuild + forward render + adjoint, all cameras",
-                   "path": "batched: one persistent forward launch; adjoint: one persistent hit-list replay "
-                           "launch and one persistent re-traversal launch over the overflow tiles; CUDA graph",
-                   "tune": tune_b.as_dict(), "l2": "flushed between timed steps (256 MiB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+        "config": bench_config(wl, world),
+        "path": "batched: one persistent forward launch; adjoint: one persistent hit-list replay "
+                "launch and one persistent re-traversal launch over the overflow tiles; CUDA graph",
+        "tune": tune_b.as_dict(), "autotune": autotune, "step_ms": step_ms, "parity": parity,
         "fwd_mrays_s": P / ms_f / 1e3 * world, "ms_per_step_fwd": ms_f,
         "fwd_bwd_mrays_s_no_graph": P / ms_fb_nograph / 1e3 * world,
         "plain": plain,

@@ -34,3 +34,20 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"]
+
+
+def test_reference_arm_config_equals_ours():
+    """Both arms print the same `config` object, so their lines describe one workload."""
+    sys.path.insert(0, ROOT)
+    import bench
+    old = sys.argv
+    sys.argv = ["bench.py", "--case", "small"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = old
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--case", "small", "--steps", "1",
+                        "--warmup", "0", "--cpu-seconds", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][0])
+    assert d["config"] == bench.bench_config(bench.make_workload(args), 1)
