@@ -91,16 +91,15 @@ __device__ __forceinline__ int64_t pack_hit_key(float hi, float tc, float tr, in
     const float bb = __fsub_rn(hi, tc);
     const float lo = __fadd_rn(__fsub_rn(tc, __fsub_rn(hi, bb)), __fsub_rn(tr, bb));
     const uint32_t hb = __float_as_uint(hi);
-    const int E = (int)(hb >> 23);  // biased exponent (hi >= 0)
-    const int sb = 32 - jb;         // residual bits (jb <= 30, so sb >= 2)
-    uint32_t sub = 1u << (sb - 1);  // lo = 0, or hi too small to resolve
-    if (E >= 24) {
-        // lo / ulp(hi) in [-1/2, 1/2] (exact: a power-of-two scale), then to [0, 2^sb)
-        const float f = __fmul_rn(lo, __uint_as_float((uint32_t)(277 - E) << 23));
-        const float sc = __fmul_rn(__fadd_rn(f, 0.5f), __uint_as_float((uint32_t)(127 + sb) << 23));
-        sub = min(__float2uint_rd(sc), (1u << sb) - 1u);
-    }
-    return (int64_t)(((uint64_t)hb << 32) | ((uint64_t)sub << jb) | (uint32_t)j);
+    // w = 1.5 + lo / ulp(hi) lies in [1, 2], where a float's mantissa is linear in its value:
+    // m = (lo / ulp(hi) + 1/2) 2^23.  The scale 2^(150 - E) (E the biased exponent of hi >= 0)
+    // is exact; exponents below 23 (t < 2^-104) are clamped, which only coarsens the residual.
+    const uint32_t E = max(hb >> 23, 23u);
+    const float w = __fmaf_rn(lo, __uint_as_float((277u - E) << 23), 1.5f);
+    const uint32_t m = min(__float_as_uint(w) - 0x3f800000u, 0x7fffffu);
+    // the top 32 - jb bits of m, placed above the id: (m << 9) keeps bit 22 of m at bit 31
+    const uint32_t low = ((m << 9) & ~((1u << jb) - 1u)) | (uint32_t)j;
+    return (int64_t)(((uint64_t)hb << 32) | low);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -1486,34 +1486,36 @@ __device__ __forceinline__ float warp_max_nonneg(float v) {
 // hits in order without compositing them, accumulating the colour S and transmittance T2 seen
 // behind its last composited hit until T2 < eps2; (S + T2 background, 1 - T2) is stored per
 // pixel for the adjoint.
-// The pending-hit buffer of the best-first forward, two layouts with one interface.  Keys are
-// kept ascending; front() is the nearest pending key (kEmptyKey when none) and last() the K-th
-// (kEmptyKey unless the buffer is full).
+// The pending-hit buffer of the best-first traversals, two layouts with one interface.  Keys are
+// kept ascending (forward) or descending (DESC: the adjoint's back-to-front replay); front() is
+// the next key to composite / replay (the empty key when none) and last() the K-th (the empty
+// key unless the buffer is full).
 //
 // RegKbuf: K 64-bit keys in registers, compare-exchange networks sized by the warp's fill.
-template <int K>
+template <int K, bool DESC = false>
 struct RegKbuf {
+    static constexpr int64_t kEmpty = DESC ? kEmptyKeyDesc : kEmptyKey;
     int64_t keys[K];
     int nk;  // occupied slots [0, nk)
     __device__ __forceinline__ explicit RegKbuf(int64_t*) {}
     __device__ __forceinline__ void reset() {
 #pragma unroll
-        for (int s = 0; s < K; ++s) keys[s] = kEmptyKey;
+        for (int s = 0; s < K; ++s) keys[s] = kEmpty;
         nk = 0;
     }
     __device__ __forceinline__ int64_t front() const { return keys[0]; }
     __device__ __forceinline__ int64_t last() const { return keys[K - 1]; }
-    // insert `key` (< last()) where `ins`; all 32 lanes call, converged
-    __device__ __forceinline__ void insert_warp(bool ins, int64_t key) { kbuf_insert_warp<K>(keys, nk, ins, key); }
+    // insert `key` (before last() in the buffer's order) where `ins`; all 32 lanes call, converged
+    __device__ __forceinline__ void insert_warp(bool ins, int64_t key) { kbuf_insert_warp<K, DESC>(keys, nk, ins, key); }
     // drop front() in the calling lanes (converged among themselves)
-    __device__ __forceinline__ void pop(unsigned group) { kbuf_pop_warp<K>(keys, nk, kEmptyKey, group); }
-    // drop every key >= cap
-    __device__ __forceinline__ void drop_from(int64_t cap) {
+    __device__ __forceinline__ void pop(unsigned group) { kbuf_pop_warp<K>(keys, nk, kEmpty, group); }
+    // drop every key at or beyond `bound` (ascending: >= bound; descending: <= bound)
+    __device__ __forceinline__ void drop_from(int64_t bound) {
         nk = 0;
 #pragma unroll
         for (int s = 0; s < K; ++s) {
-            if (keys[s] >= cap) keys[s] = kEmptyKey;
-            nk += keys[s] != kEmptyKey;
+            if (DESC ? keys[s] <= bound : keys[s] >= bound) keys[s] = kEmpty;
+            nk += keys[s] != kEmpty;
         }
     }
 };
@@ -1523,11 +1525,12 @@ struct RegKbuf {
 // 32 distinct 8-byte words whatever their ring positions: no bank conflicts.  Only the head,
 // the fill and copies of front() and last() live in registers, which frees the 64 registers
 // of the register buffer for occupancy.  An insert shifts the keys after the new one by one
-// slot (insertion order is nearly ascending in best-first order, so shifts are short); a pop
+// slot (insertion order is nearly sorted in best-first order, so shifts are short); a pop
 // advances the head.
-template <int K>
+template <int K, bool DESC = false>
 struct SmemKbuf {
     static_assert((K & (K - 1)) == 0, "ring size must be a power of two");
+    static constexpr int64_t kEmpty = DESC ? kEmptyKeyDesc : kEmptyKey;
     int64_t* col;
     int head, nk;
     int64_t fr, lst;
@@ -1536,7 +1539,7 @@ struct SmemKbuf {
     __device__ __forceinline__ void reset() {
         head = 0;
         nk = 0;
-        fr = lst = kEmptyKey;
+        fr = lst = kEmpty;
     }
     __device__ __forceinline__ int64_t front() const { return fr; }
     __device__ __forceinline__ int64_t last() const { return lst; }
@@ -1545,26 +1548,26 @@ struct SmemKbuf {
         int i = nk < K ? nk : K - 1;  // a full ring drops its last key
         while (i > 0) {
             const int64_t v = at(i - 1);
-            if (v < key) break;
+            if (DESC ? v > key : v < key) break;
             at(i) = v;
             --i;
         }
         at(i) = key;
         if (nk < K) ++nk;
         if (i == 0) fr = key;
-        lst = nk == K ? at(K - 1) : kEmptyKey;
+        lst = nk == K ? at(K - 1) : kEmpty;
     }
     __device__ __forceinline__ void pop(unsigned) {
         head = (head + 1) & (K - 1);
         --nk;
-        fr = nk > 0 ? at(0) : kEmptyKey;
-        lst = kEmptyKey;
+        fr = nk > 0 ? at(0) : kEmpty;
+        lst = kEmpty;
     }
-    __device__ __forceinline__ void drop_from(int64_t cap) {
+    __device__ __forceinline__ void drop_from(int64_t bound) {
         const int before = nk;
-        while (nk > 0 && at(nk - 1) >= cap) --nk;
-        if (nk == 0) fr = kEmptyKey;
-        if (nk != before) lst = kEmptyKey;
+        while (nk > 0 && (DESC ? at(nk - 1) <= bound : at(nk - 1) >= bound)) --nk;
+        if (nk == 0) fr = kEmpty;
+        if (nk != before) lst = kEmpty;
     }
 };
 
@@ -1819,14 +1822,22 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                         : make_float4(0.f, 0.f, 0.f, -1.f);
 }
 
-template <int K, bool COUNT, int W, bool DEPTH>
+// SMEMK: the pending hits in a descending shared-memory ring (SmemKbuf; kb_col = this lane's
+// column of its warp's 32 K-slot block) instead of registers.
+template <int K, bool COUNT, int W, bool DEPTH, bool SMEMK = false>
 __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec, const float4* __restrict__ sph, const NodeSrc& nodes,
                                                   const TraceParams& P, const float3 o, const float3 d,
-                                                  float T_final, int64_t last_key, int n_hits, const Upstream& g, float4* __restrict__ gtmp, Counters& cnt, int* err) {
+                                                  float T_final, int64_t last_key, int n_hits, const Upstream& g,
+                                                  float4* __restrict__ gtmp, Counters& cnt, int* err,
+                                                  int64_t* kb_col = nullptr) {
+    using KB = std::conditional_t<SMEMK, SmemKbuf<K, true>, RegKbuf<K, true>>;
+    KB kb(kb_col);
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const int jb = key_id_bits(P.n_gauss);  // id bits of the ordering keys
+    // camera rays share their origin: the leaf pre-test bounds the warp's rays by a cone
+    const RayCone cone = warp_ray_cone(o, d);
     const float NINF = __int_as_float(0xff800000);
     const float INF = __int_as_float(0x7f800000);
     constexpr uint32_t kFloorJ = kKeyLowMax;  // the largest key at a given t
@@ -1841,26 +1852,20 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         }
         if (COUNT && remaining > 0) cnt.rounds++;
         bool active = remaining > 0;
-        int64_t keys[K];
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-            keys[s] = kEmptyKeyDesc;
-        }
-        int nk = 0;  // pending keys (slots [0, nk))
+        kb.reset();
         int64_t floor_key = -1;
         const int64_t pass_hi = hi_key;  // where this pass starts (from the back)
         const float thi = key_t(hi_key);
         bool stop = false;
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
-            const int64_t key = keys[0];
+            const int64_t key = kb.front();
             const int j = key_j(key, jb);
             adjoint_hit<DEPTH>(rec, j, o, d, P, adj, g, vout);
             jout = j;
             --remaining;
             hi_key = key;
             if (COUNT) cnt.hits++;
-            kbuf_pop_front<K>(keys, kEmptyKeyDesc);
-            --nk;
+            kb.pop(__activemask());
         };
         // warp-uniform replay: every lane takes part in the aggregated scatter
         auto replay_while = [&](auto cond) {
@@ -1876,12 +1881,9 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         auto drop_floor = [&](float x) {  // a node with packet exit x was dropped (kept list full)
             if (active) {
                 floor_key = max(floor_key, pack_key(fmaxf(x, 0.f), kFloorJ));
-                nk = 0;
-#pragma unroll
-                for (int s = 0; s < K; ++s) {
-                    if (keys[s] <= floor_key) keys[s] = kEmptyKeyDesc;
-                    nk += keys[s] != kEmptyKeyDesc;
-                }
+                // pending hits at or below the new floor may be followed by hits of the dropped
+                // subtree: give them back (the next pass finds them again)
+                kb.drop_from(floor_key);
             }
         };
         WarpQueue q;
@@ -1900,8 +1902,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             bool need = false;
             if (popped && active) {
                 const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
-                const bool full = keys[K - 1] != kEmptyKeyDesc;
-                const float tK = full ? key_t(keys[K - 1]) : NINF;
+                const int64_t kK = kb.last();
+                const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
                 if (x_node >= tfl) {
                     if (x_node < tK) floor_key = max(floor_key, pack_key(fmaxf(x_node, 0.f), kFloorJ));
                     else need = true;
@@ -1926,8 +1928,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 }
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
-                    const bool full = keys[K - 1] != kEmptyKeyDesc;
-                    const float tK = full ? key_t(keys[K - 1]) : NINF;
+                    const int64_t kK = kb.last();
+                    const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         h[c] = ch.ref[c] != kEmptyRef && en[c] <= thi && x[c] >= tfl && x[c] >= en[c];
@@ -1943,7 +1945,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     const bool want = h[c] && rr < 0;
                     if (__any_sync(FULL, want)) {
                         const int start = ~rr, num = leaf_count(nodes, ~rr, ch.cnt[c]);
-                        const uint32_t mask = leaf_sphere_mask(sph, start, num, want, o, d);
+                        const uint32_t mask = cone.ok ? leaf_sphere_mask_cone(sph, start, num, want, o, d, cone)
+                                                      : leaf_sphere_mask(sph, start, num, want, o, d);
                         uint32_t todo = __reduce_or_sync(FULL, mask);
                         while (todo) {
                             const int g = __ffs(todo) - 1;
@@ -1962,8 +1965,9 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                 if (hh.hit) {
                                     const int64_t key = hit_key(hh, P.sort_key, qq, jb);
                                     if (key < hi_key && key > floor_key) {
-                                        if (key > keys[K - 1]) {
-                                            if (keys[K - 1] != kEmptyKeyDesc) floor_key = keys[K - 1];
+                                        const int64_t kK = kb.last();
+                                        if (key > kK) {
+                                            if (kK != kEmptyKeyDesc) floor_key = kK;
                                             ins = true;
                                             ikey = key;
                                             if (COUNT) cnt.inserted++;
@@ -1973,7 +1977,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                     }
                                 }
                             }
-                            if (__any_sync(FULL, ins)) kbuf_insert_warp<K, true>(keys, nk, ins, ikey);
+                            if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
                         }
                     }
                 }
@@ -1982,8 +1986,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 for (int c = 0; c < W; ++c) in[c] = h[c] && ch.ref[c] >= 0;
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
-                    const bool full = keys[K - 1] != kEmptyKeyDesc;
-                    const float tK = full ? key_t(keys[K - 1]) : NINF;
+                    const int64_t kK = kb.last();
+                    const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         if (in[c] && x[c] < tfl) in[c] = false;
@@ -2007,7 +2011,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             qtop = wq_extreme_key<true>(q);
             // -inf when nothing is left: replay everything pending
             const float bound = fmaxf(wq_key_priority<true>(qtop), wd_best);
-            replay_while([&] { return active && remaining > 0 && keys[0] != kEmptyKeyDesc && key_t(keys[0]) > bound; });
+            replay_while([&] { return active && remaining > 0 && kb.front() != kEmptyKeyDesc && key_t(kb.front()) > bound; });
             active = active && remaining > 0;
             if (!popped || !__any_sync(FULL, active)) break;
         }
