@@ -28,8 +28,10 @@ constexpr int kMaxHitList = 4096;         // largest per-ray hit list
 constexpr int kNumStats = 10;             // uint64 counters of rs_render_stats        // staged top nodes (64 B each) in shared memory
 constexpr int kTopRef = 0x40000000;       // node reference kTopRef + s = staged slot s
 constexpr int kEmptyRef = INT32_MIN;      // empty child slot of a wide node         // >= depth of a radix tree over 64-bit codes + 32-bit ids
-constexpr int64_t kEmptyKey = INT64_MAX;  // empty slot of an ascending k-buffer
-constexpr int64_t kEmptyKeyDesc = -1;     // empty slot of a descending k-buffer
+// Empty slots sort after (ascending) or before (descending) every key, and their time half is
+// +inf (ascending) or -inf (descending), so key_t() of an empty slot needs no test.
+constexpr int64_t kEmptyKey = (int64_t)0x7f800000ffffffffull;       // ascending k-buffer
+constexpr int64_t kEmptyKeyDesc = (int64_t)0xff80000000000000ull;   // descending k-buffer
 
 // device error word bits
 enum : int {

@@ -89,6 +89,13 @@ __device__ __forceinline__ uint32_t leaf_sphere_mask(const float4* __restrict__ 
     return mask;
 }
 
+// the hardware's approximate square root (relative error below 2^-22)
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // The rays of a warp that share one origin (a camera's tile) as a cone: axis, cos and sin of
 // the half-angle, widened so that rounding cannot make it narrower than the rays.
 struct RayCone {
@@ -141,11 +148,11 @@ __device__ __forceinline__ uint32_t leaf_sphere_mask_cone(const float4* __restri
         mine = __ldg(sph + start + lane);
         const float wx = mine.x - o.x, wy = mine.y - o.y, wz = mine.z - o.z;
         const float L2 = wx * wx + wy * wy + wz * wz;
-        const float r = sqrtf(mine.w) * 1.0001f + 1e-6f * sqrtf(L2);
+        const float r = sqrt_approx(mine.w) * 1.0001f + 1e-6f * sqrt_approx(L2);
         const float t = wx * cone.ax.x + wy * cone.ax.y + wz * cone.ax.z;
         const float cx = wy * cone.ax.z - wz * cone.ax.y, cy = wz * cone.ax.x - wx * cone.ax.z;
         const float cz = wx * cone.ax.y - wy * cone.ax.x;
-        const float dperp = sqrtf(cx * cx + cy * cy + cz * cz);
+        const float dperp = sqrt_approx(cx * cx + cy * cy + cz * cz);
         reach = L2 <= r * r || (t > -r && dperp * cone.cth - t * cone.sth <= r);
     }
     uint32_t cand = __ballot_sync(FULL, reach);
@@ -1687,9 +1694,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             // a lane needs the node unless its (conservative) entry lies past its bounds
             bool need = false;
             if (popped && active) {
-                const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                const float tcap = key_t(cap);
                 const int64_t kK = kb.last();
-                const float tK = kK != kEmptyKey ? key_t(kK) : INF;
+                const float tK = key_t(kK);
                 if (e_node <= tcap) {
                     if (e_node > tK) cap = min(cap, pack_key(fmaxf(e_node, 0.f), 0));
                     else need = true;
@@ -1715,9 +1722,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     h[c] = false;
                 }
                 if (need) {
-                    const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                    const float tcap = key_t(cap);
                     const int64_t kK = kb.last();
-                    const float tK = kK != kEmptyKey ? key_t(kK) : INF;
+                    const float tK = key_t(kK);
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         h[c] = ch.ref[c] != kEmptyRef && e[c] <= fminf(x[c], tcap);
@@ -1767,7 +1774,8 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                                     }
                                 }
                             }
-                            if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
+                            if (SMEMK) kb.insert_warp(ins, ikey);  // per lane: no vote needed
+                            else if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
                         }
                     }
                 }
@@ -1775,9 +1783,9 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
 #pragma unroll
                 for (int c = 0; c < W; ++c) in[c] = h[c] && ch.ref[c] >= 0;
                 if (need) {
-                    const float tcap = cap == kEmptyKey ? INF : key_t(cap);
+                    const float tcap = key_t(cap);
                     const int64_t kK = kb.last();
-                    const float tK = kK != kEmptyKey ? key_t(kK) : INF;
+                    const float tK = key_t(kK);
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         if (in[c] && e[c] > tcap) in[c] = false;
@@ -1801,7 +1809,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
             qtop = wq_extreme_key<false>(q);
             // +inf when nothing is left: composite all pending
             const float bound = fminf(wq_key_priority<false>(qtop), wd_best);
-            while (active && !done && kb.front() != kEmptyKey && key_t(kb.front()) < bound) composite_front();
+            while (active && !done && key_t(kb.front()) < bound) composite_front();
             active = active && !done;
             if (!popped || !__any_sync(FULL, active)) break;
         }
@@ -1909,7 +1917,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             if (popped && active) {
                 const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                 const int64_t kK = kb.last();
-                const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
+                const float tK = key_t(kK);  // -inf when the buffer is not full
                 if (x_node >= tfl) {
                     if (x_node < tK) floor_key = max(floor_key, pack_key(fmaxf(x_node, 0.f), kFloorJ));
                     else need = true;
@@ -1935,7 +1943,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                     const int64_t kK = kb.last();
-                    const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
+                    const float tK = key_t(kK);  // -inf when the buffer is not full
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         h[c] = ch.ref[c] != kEmptyRef && en[c] <= thi && x[c] >= tfl && x[c] >= en[c];
@@ -1983,7 +1991,8 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                     }
                                 }
                             }
-                            if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
+                            if (SMEMK) kb.insert_warp(ins, ikey);  // per lane: no vote needed
+                            else if (__any_sync(FULL, ins)) kb.insert_warp(ins, ikey);
                         }
                     }
                 }
@@ -1993,7 +2002,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                 if (need) {
                     const float tfl = floor_key < 0 ? P.t_near : fmaxf(P.t_near, key_t(floor_key));
                     const int64_t kK = kb.last();
-                    const float tK = kK != kEmptyKeyDesc ? key_t(kK) : NINF;
+                    const float tK = key_t(kK);  // -inf when the buffer is not full
 #pragma unroll
                     for (int c = 0; c < W; ++c) {
                         if (in[c] && x[c] < tfl) in[c] = false;
@@ -2017,7 +2026,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             qtop = wq_extreme_key<true>(q);
             // -inf when nothing is left: replay everything pending
             const float bound = fmaxf(wq_key_priority<true>(qtop), wd_best);
-            replay_while([&] { return active && remaining > 0 && kb.front() != kEmptyKeyDesc && key_t(kb.front()) > bound; });
+            replay_while([&] { return active && remaining > 0 && key_t(kb.front()) > bound; });
             active = active && remaining > 0;
             if (!popped || !__any_sync(FULL, active)) break;
         }
