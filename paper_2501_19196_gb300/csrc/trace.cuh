@@ -178,16 +178,18 @@ struct Children {
     int ref[W], cnt[W];
 };
 
+// STAGED = false: the caller stages no nodes (no shared-memory branch)
+template <bool STAGED = true>
 __device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& n0, float4& n1, float4& n2,
                                            float4& n3) {
-    const bool ok = node >= kTopRef ? (node - kTopRef) < ns.n_top : (node >= 0 && node < ns.n_nodes);
+    const bool ok = (STAGED && node >= kTopRef) ? (node - kTopRef) < ns.n_top : (node >= 0 && node < ns.n_nodes);
     if (!ok) {  // corrupt reference: report, and present a node without children
         atomicOr(ns.err, kErrIndex);
         n0 = n1 = n2 = make_float4(0.f, 0.f, 0.f, 0.f);
         n3 = make_float4(__int_as_float(kEmptyRef), __int_as_float(kEmptyRef), __int_as_float(0), __int_as_float(0));
         return;
     }
-    if (node >= kTopRef) {
+    if (STAGED && node >= kTopRef) {
         const float4* p = ns.s + 4 * (node - kTopRef);
         n0 = p[0];
         n1 = p[1];
@@ -201,13 +203,13 @@ __device__ __forceinline__ void fetch_node(const NodeSrc& ns, int node, float4& 
     }
 }
 
-template <int W>
+template <int W, bool STAGED = true>
 __device__ __forceinline__ void fetch_children(const NodeSrc& ns, int node, Children<W>& ch);
 
-template <>
-__device__ __forceinline__ void fetch_children<2>(const NodeSrc& ns, int node, Children<2>& ch) {
+template <bool STAGED>
+__device__ __forceinline__ void fetch_children2(const NodeSrc& ns, int node, Children<2>& ch) {
     float4 n0, n1, n2, n3;
-    fetch_node(ns, node, n0, n1, n2, n3);
+    fetch_node<STAGED>(ns, node, n0, n1, n2, n3);
     ch.lo[0][0] = n0.x; ch.hi[0][0] = n0.y; ch.lo[1][0] = n0.z; ch.hi[1][0] = n0.w;
     ch.lo[0][1] = n1.x; ch.hi[0][1] = n1.y; ch.lo[1][1] = n1.z; ch.hi[1][1] = n1.w;
     ch.lo[2][0] = n2.x; ch.hi[2][0] = n2.y; ch.lo[2][1] = n2.z; ch.hi[2][1] = n2.w;
@@ -216,7 +218,17 @@ __device__ __forceinline__ void fetch_children<2>(const NodeSrc& ns, int node, C
 }
 
 template <>
-__device__ __forceinline__ void fetch_children<4>(const NodeSrc& ns, int node, Children<4>& ch) {
+__device__ __forceinline__ void fetch_children<2, true>(const NodeSrc& ns, int node, Children<2>& ch) {
+    fetch_children2<true>(ns, node, ch);
+}
+
+template <>
+__device__ __forceinline__ void fetch_children<2, false>(const NodeSrc& ns, int node, Children<2>& ch) {
+    fetch_children2<false>(ns, node, ch);
+}
+
+template <>
+__device__ __forceinline__ void fetch_children<4, true>(const NodeSrc& ns, int node, Children<4>& ch) {
     if (node < 0 || node >= ns.n_nodes) {
         atomicOr(ns.err, kErrIndex);
 #pragma unroll
@@ -1326,7 +1338,7 @@ struct WarpQueue {
 
 template <bool MAXQ>
 __device__ __forceinline__ uint32_t wq_empty() {
-    return MAXQ ? 0u : 0xffffffffu;
+    return MAXQ ? 0u : 0x7f80007fu;  // min-queue: +inf with no valid slot id (ids < 64)
 }
 
 template <bool MAXQ>
@@ -1398,7 +1410,7 @@ __device__ __forceinline__ bool wq_pop_known(WarpQueue& q, uint32_t v, float& pr
 // the priority of extreme key v: +inf (min-queue) / -inf (max-queue) for an empty queue
 template <bool MAXQ>
 __device__ __forceinline__ float wq_key_priority(uint32_t v) {
-    if (v == wq_empty<MAXQ>()) return MAXQ ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+    if (MAXQ && v == wq_empty<MAXQ>()) return __int_as_float(0xff800000);  // min-queue: the empty key reads +inf
     return __uint_as_float(v & ~0x7fu);
 }
 
@@ -1709,7 +1721,7 @@ __device__ __forceinline__ void trace_forward_bf(const float4* __restrict__ rec,
                     break;
                 }
                 Children<W> ch;
-                fetch_children<W>(nodes, node, ch);
+                fetch_children<W, !SMEMK>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
                 if (COUNT && lane == 0) cnt.wnodes++;
                 float e[W], x[W];
@@ -1930,7 +1942,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                     break;
                 }
                 Children<W> ch;
-                fetch_children<W>(nodes, node, ch);
+                fetch_children<W, !SMEMK>(nodes, node, ch);
                 if (COUNT && need) cnt.nodes++;
                 if (COUNT && lane == 0) cnt.wnodes++;
                 float en[W], x[W];
