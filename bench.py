@@ -32,14 +32,15 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s fwd and fwd+bwd at 1M Gaussians, batched vs plain, at oracle tolerance"
 L2_FLUSH_BYTES = 256 << 20
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at the full workload (one capture,
-# profiles/k_render_dram_traffic_1m_gaussians_16cams.md): the forward kernel, and the hit-list
-# replay for the adjoint.  Reported only while the kernel sources are unchanged (hash).
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the forward and of the
+# hit-list replay on two 640x416 cameras of the same scene (532,480 rays), scaled to a launch of
+# the 16-camera workload by its rays (x 22.615; profiles/k_render_fwd_k_replay_list_dram_traffic_
+# 1m_gaussians_2x640x416.md).  Reported only while the kernel sources are unchanged (hash).
 KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
-TRAFFIC = {"kernels": "b4d0d7e12cc0a33d", "fwd_bytes": 6.16e9, "bwd_bytes": 5.25e9}
+TRAFFIC = {"kernels": "fb9bdeae8d7df176", "fwd_bytes": 5.961e9, "bwd_bytes": 6.349e9}
 # fraction of cycles with an instruction issued (smsp__issue_active.avg.pct_of_peak_sustained_active)
 # of the forward and the list replay, from the small-case --set full profile of the same sources
-ISSUE_ACTIVE = {"kernels": "", "fwd": None, "bwd": None}
+ISSUE_ACTIVE = {"kernels": "fb9bdeae8d7df176", "fwd": 0.6588, "bwd": 0.3688}
 
 
 def parse():
