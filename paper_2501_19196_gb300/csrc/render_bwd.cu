@@ -78,11 +78,13 @@ __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
 // forward does (SmemKbuf, descending): the register buffer held 64 of its 167 registers (3 CTAs
 // of 4 warps per SM).  With the rings it runs 4 CTAs per SM at 123 registers without spills
 // (measured 1.7x faster than the register buffer; 5 and 6 CTAs per SM spill and were slower).
-// It does not stage top nodes (the rings take that shared memory).
+// Each lane also keeps a list of 16 finalised keys in shared memory, replayed densely (48 KB per
+// CTA with both).  It does not stage top nodes (the rings take that shared memory).
 constexpr bool kBwdSmemKbuf = true;
 
+// rings of K pending keys and lists of 16 finalised keys per lane
 template <int K>
-static size_t bwd_ring_smem_bytes(int block) { return (size_t)(block / 32) * K * 32 * sizeof(int64_t); }
+static size_t bwd_ring_smem_bytes(int block) { return (size_t)(block / 32) * (K + 16) * 32 * sizeof(int64_t); }
 
 template <int K, bool PERSIST, bool COUNT, int MODE, bool DEPTH, bool SMEMK = false>
 __global__ void __launch_bounds__(128, SMEMK ? 4 : 1) k_render_bwd(FwdArgs A, BwdArgs B) {
@@ -95,7 +97,11 @@ __global__ void __launch_bounds__(128, SMEMK ? 4 : 1) k_render_bwd(FwdArgs A, Bw
                      A.n_top, A.P.n_gauss, A.err};
     const int lane = threadIdx.x & 31;
     int64_t* kb_col = nullptr;  // this lane's column of its warp's ring block
-    if (SMEMK) kb_col = reinterpret_cast<int64_t*>(s_top) + (threadIdx.x >> 5) * (K * 32) + lane;
+    int64_t* fin_col = nullptr;  // this lane's column of its warp's finalised-key block
+    if (SMEMK) {
+        kb_col = reinterpret_cast<int64_t*>(s_top) + (threadIdx.x >> 5) * (K * 32) + lane;
+        fin_col = reinterpret_cast<int64_t*>(s_top) + (blockDim.x >> 5) * (K * 32) + (threadIdx.x >> 5) * (16 * 32) + lane;
+    }
     // with a hit list, only the tiles the list replay found overflowing are re-traversed
     const int64_t n_tiles = B.ovf ? (int64_t)min((unsigned long long)B.ovf_cap, A.queue[3]) : A.total_tiles;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(128, SMEMK ? 4 : 1) k_render_bwd(FwdArgs A, Bw
             trace_backward_bf<K, COUNT, 4, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
         else if (MODE == 2 && SMEMK)
             trace_backward_bf<K, COUNT, 2, DEPTH, true>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err,
-                                                        kb_col);
+                                                        kb_col, fin_col);
         else if (MODE == 2)
             trace_backward_bf<K, COUNT, 2, DEPTH>(A.rec, A.sph, ns, A.P, o, d, Tf, lk, nt, g, B.gtmp, cnt, A.err);
         else if (MODE == 1)

@@ -1849,7 +1849,7 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
                                                   const TraceParams& P, const float3 o, const float3 d,
                                                   float T_final, int64_t last_key, int n_hits, const Upstream& g,
                                                   float4* __restrict__ gtmp, Counters& cnt, int* err,
-                                                  int64_t* kb_col = nullptr) {
+                                                  int64_t* kb_col = nullptr, int64_t* fin_col = nullptr) {
     using KB = std::conditional_t<SMEMK, SmemKbuf<K, true>, RegKbuf<K, true>>;
     KB kb(kb_col);
     const unsigned FULL = 0xffffffffu;
@@ -1877,6 +1877,44 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
         const int64_t pass_hi = hi_key;  // where this pass starts (from the back)
         const float thi = key_t(hi_key);
         bool stop = false;
+        // SMEMK: a hit whose key passes the bound is finalised (taken from the ring into a
+        // per-lane list of up to kFin keys in shared memory, in replay order); the lists are
+        // replayed densely, all lanes at once, when one fills or the pass ends
+        constexpr int kFin = 16;
+        int nf = 0;
+        auto fin_at = [&](int i) -> int64_t& { return fin_col[32 * i]; };
+        auto replay_fin = [&]() {
+            int i = 0;
+            while (__any_sync(0xffffffffu, i < nf)) {
+                int jout = -1;
+                float4 vout[4];
+                if (i < nf) {
+                    jout = key_j(fin_at(i), jb);
+                    adjoint_hit<DEPTH>(rec, jout, o, d, P, adj, g, vout);
+                    if (COUNT) cnt.hits++;
+                }
+                ++i;
+                if (jout >= 0) {
+                    float4* gp = gtmp + 4 * jout;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) atomicAdd(gp + q, vout[q]);
+                }
+            }
+            nf = 0;
+        };
+        auto finalize_while = [&](auto cond) {
+            while (true) {
+                while (nf < kFin && cond()) {
+                    const int64_t key = kb.front();
+                    fin_at(nf++) = key;
+                    --remaining;
+                    hi_key = key;
+                    kb.pop(0u);
+                }
+                if (!__any_sync(0xffffffffu, nf == kFin && cond())) break;
+                replay_fin();
+            }
+        };
         auto replay_contrib = [&](int& jout, float4 (&vout)[4]) {
             const int64_t key = kb.front();
             const int j = key_j(key, jb);
@@ -2038,10 +2076,12 @@ __device__ __forceinline__ void trace_backward_bf(const float4* __restrict__ rec
             qtop = wq_extreme_key<true>(q);
             // -inf when nothing is left: replay everything pending
             const float bound = fmaxf(wq_key_priority<true>(qtop), wd_best);
-            replay_while([&] { return active && remaining > 0 && key_t(kb.front()) > bound; });
+            if constexpr (SMEMK) finalize_while([&] { return active && remaining > 0 && key_t(kb.front()) > bound; });
+            else replay_while([&] { return active && remaining > 0 && key_t(kb.front()) > bound; });
             active = active && remaining > 0;
             if (!popped || !__any_sync(FULL, active)) break;
         }
+        if constexpr (SMEMK) replay_fin();
         if (__any_sync(FULL, stop)) break;
         if (active && remaining > 0 && floor_key < 0) {
             atomicOr(err, kErrReplayMismatch);
