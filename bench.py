@@ -38,9 +38,13 @@ L2_FLUSH_BYTES = 256 << 20
 # 1m_gaussians_2x640x416.md).  Reported only while the kernel sources are unchanged (hash).
 KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
 TRAFFIC = {"kernels": "066672b1652eb288", "fwd_bytes": 5.969e9, "bwd_bytes": 6.347e9}
-# fraction of cycles with an instruction issued (smsp__issue_active.avg.pct_of_peak_sustained_active)
-# of the forward and the list replay, from the small-case --set full profile of the same sources
+# from the small-case --set full profiles of the same sources, per kernel (forward, list replay):
+# the fraction of cycles with an instruction issued (smsp__issue_active), the L2 hit rate
+# (lts__t_sector_hit_rate) and the active lanes per warp instruction over 32
+# (smsp__thread_inst_executed_per_inst_executed / 32, the warp execution efficiency)
 ISSUE_ACTIVE = {"kernels": "066672b1652eb288", "fwd": 0.6597, "bwd": 0.3688}
+L2_HIT = {"kernels": "066672b1652eb288", "fwd": 0.8418, "bwd": 0.6809}
+WARP_EFF = {"kernels": "066672b1652eb288", "fwd": 23.43 / 32, "bwd": 25.68 / 32}
 
 
 def parse():
@@ -627,8 +631,9 @@ def run_ours(args):
                 "frac": achieved / hbm, "frac_kind": "touched (algorithmic) bytes over the HBM copy peak",
                 "traffic": traffic,
                 "dram_frac": (traffic / (kms[dom] * 1e-3) / 1e9 / hbm) if traffic else None,
-                "issue_active": ISSUE_ACTIVE.get("fwd" if dom == "fwd" else "bwd")
-                if ISSUE_ACTIVE.get("kernels") == src_hash() else None,
+                "issue_active": ISSUE_ACTIVE.get(dom) if ISSUE_ACTIVE.get("kernels") == src_hash() else None,
+                "l2_hit_rate": L2_HIT.get(dom) if L2_HIT.get("kernels") == src_hash() else None,
+                "warp_exec_efficiency": WARP_EFF.get(dom) if WARP_EFF.get("kernels") == src_hash() else None,
                 "kernel": "adjoint: k_replay_list + k_render_bwd + k_finalize" if dom == "bwd"
                 else "k_render_fwd (persistent)", "peak_source": f"{peak_kind} hbm_gbs",
                 "algorithmic_bytes_per_launch": dom_bytes, "kernel_ms": kms[dom],
@@ -712,6 +717,15 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "Mrays/s", "cores": thr, "kind": "oracle",
                "sample": f"{nr} stratified rays of the same workload, fwd + gradient, FP64 brute force, {dt:.1f} s"}
 
+    # the LBVH rebuild, reported apart: algorithmic bytes per Gaussian (bounds 12; Morton codes
+    # 12 read + 12 written; 8 radix passes of 8 B histogram reads and 24 B scatter traffic;
+    # records 56 read + 88 written; Karras and refit about 160 per node) over its event time
+    build_bytes = n * (12 + 24 + 8 * 32 + 144 + 160)
+    build = {"ms": kms["build"], "algorithmic_bytes": build_bytes,
+             "achieved_gbs": build_bytes / (kms["build"] * 1e-3) / 1e9,
+             "frac_of_hbm": build_bytes / (kms["build"] * 1e-3) / 1e9 / hbm,
+             "launches": 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3 + (1 if tune_b.smem_nodes > 0 else 0),
+             "bound": "launch and latency (31 short launches, 1M-element kernels)"}
     # bounds init, bounds, morton, 3 per sort pass, records, karras, refit, top-node staging
     launches_build = 3 + 3 * (4 if tune_b.morton_bits == 10 else 8) + 3 + (1 if tune_b.smem_nodes > 0 else 0)
     # forward; adjoint: list replay + re-traversal of the overflow tiles (or one re-traversal
@@ -745,7 +759,7 @@ def run_ours(args):
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
         "kernel_ms": kms,
         "adjoint_without_hit_lists": replay, "training_step": train, "mirror_scene": mirror,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+        "roofline": roofline, "build": build, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
     if rank == 0:
