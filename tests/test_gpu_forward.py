@@ -357,3 +357,41 @@ def test_rays_starting_inside_many_overlapping_boxes():
     for tune in (dict(), dict(traversal=1), dict(kbuf=8)):
         g = gpu_render(sc, cams, prm, tune=native.default_tune(**tune))  # raises on a loop-guard error
         compare_image(g, ora, pixel_index(cams, cam, px, py), max_masked=0.03, label=f"dense overlap {tune}")
+
+
+# ------------------------------------------------------------------------------------------
+# ordering below an FP32 ulp (the hit keys' residual)
+# ------------------------------------------------------------------------------------------
+def test_hits_closer_than_an_ulp_are_ordered_by_their_accurate_entry():
+    """Pairs of small spheres on one pixel ray each, 0.3 to 0.45 ulp of t apart in depth: their
+    FP32 entries often round to the same float, so only the keys' sub-ulp residual orders them.
+    The farther sphere of each pair comes first in the caller's order and both share a Morton
+    code (a distant third sphere sets the bounds), so an id tie-break would composite it first.
+    The spacing exceeds the oracle's TIE band, so every pixel has one correct value."""
+    cam = scenes.look_at_camera((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 7, 7, 40.0)
+    cidx, px, py = scenes.pixel_grid(cam)
+    o, d = oracle.raygen_f32(cam, cidx, px, py)
+    rng = np.random.default_rng(8)
+    s = 0.004
+    means, rgb = [], []
+    for r in range(len(px)):
+        t0 = 4.0 + rng.uniform(-0.05, 0.05)
+        ulp = np.spacing(np.float32(t0 - np.sqrt(Q) * s))
+        sep = rng.uniform(0.3, 0.45) * float(ulp)
+        near = o[r].astype(np.float64) + t0 * d[r].astype(np.float64)
+        far = o[r].astype(np.float64) + (t0 + sep) * d[r].astype(np.float64)
+        means += [far, near]           # the farther one first in the caller's order
+        rgb += [(1.0, 0.0, 0.0), (0.0, 0.0, 1.0)]
+    means.append((50.0, 50.0, 50.0))   # far away: sets the Morton bounds, hit by no ray
+    rgb.append((0.5, 0.5, 0.5))
+    n = len(means)
+    sc = scenes.Scene(np.asarray(means, np.float32), np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                      np.full((n, 3), s, np.float32), np.full(n, 0.8, np.float32), np.asarray(rgb, np.float32))
+    prm = params()
+    g = gpu_render(sc, cam, prm)
+    ora = oracle_pixels(sc, cam, cidx, px, py, prm)
+    assert np.all(ora["n_hits"] == 2)
+    assert np.all(ora["mask"] == 0), "the oracle flags a pair: the spacing is inside its TIE band"
+    # the nearer (blue) sphere first: blue 0.8, red 0.2 * 0.8
+    np.testing.assert_allclose(ora["rgb"][:, 2], 0.8, atol=1e-6)
+    compare_image(g, ora, pixel_index(cam, cidx, px, py), max_masked=0.0, label="sub-ulp ordering")
