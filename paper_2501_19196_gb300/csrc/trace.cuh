@@ -2,22 +2,24 @@
 // (render_fwd.cu, render_bwd.cu): ray/box and ray/ellipsoid tests, k-buffers, the warp
 // node queue, the per-ray and warp-packet traversals, and the per-hit adjoint.
 //
-// Forward (a7-a9): each lane traces one camera ray.  A round traverses the LBVH with a
-// register k-buffer of the K nearest hits whose (t1, id) key lies beyond the last composited
-// key (nodes whose box entry lies past the K-th key are pruned), then composites those hits
-// front to back (Eq. 3) with alpha = opacity * exp(-D2/2) (Prop. 2), stopping after the hit
-// that brings T below eps1 or at k_max hits (Sec. 3).  A full buffer starts the next round.
-// Per ray it stores T_final, the last composited key and the hit count (16 B).
+// Forward (a7-a9): each lane traces one camera ray.  A pass traverses the LBVH (by default
+// best first over warp packets) with a buffer of pending hits ordered by their (t, residual,
+// id) key beyond the last composited key; a pending hit is composited front to back (Eq. 3)
+// with alpha = opacity * exp(-D2/2) (Prop. 2) as soon as no unvisited box can hold an earlier
+// hit, and the ray stops after the hit that brings T below eps1 or at k_max hits (Sec. 3).  A
+// buffer that overflows caps the pass and a further pass resumes after the last composited
+// key.  Per ray it stores T_final, the last composited key and the hit count (16 B), and the
+// ids of its first hit_list composited hits.
 //
-// Adjoint (a10): the same traversal with a descending k-buffer of the K farthest hits below
-// an upper key replays the composited hits back to front.  The transmittance before each hit
-// is recovered as T_i = T_{i+1} / (1 - alpha_i) from the stored T_final (the forward's
-// (1 - alpha_i) is recomputed bit for bit, so the rounding cancels), and the colour behind a
-// hit follows U_{i-1} = alpha_i c_i + (1 - alpha_i) U_i, giving dC/dalpha_i = T_i (c_i - U_i)
-// without the division of App. A.4/A.5.  The chain through D2 (App. A.6) uses the envelope
-// form dD2/dM = 2 p v^T, dD2/dm = -2 M^T p; per-hit contributions go to a 16-float-per-
-// Gaussian accumulator with float4 atomics, and a finalize kernel maps dL/dM to the
-// quaternion and scales through M = S^-1 R(q)^T.
+// Adjoint (a10): from the hit list, or by the same traversal mirrored (a descending buffer of
+// pending hits below an upper key), the composited hits are replayed back to front.  The
+// transmittance before each hit is recovered as T_i = T_{i+1} / (1 - alpha_i) from the stored
+// T_final (the forward's (1 - alpha_i) is recomputed bit for bit, so the rounding cancels),
+// and the colour behind a hit follows U_{i-1} = alpha_i c_i + (1 - alpha_i) U_i, giving
+// dC/dalpha_i = T_i (c_i - U_i) without the division of App. A.4/A.5.  The chain through D2
+// (App. A.6) uses the envelope form dD2/dM = 2 p v^T, dD2/dm = -2 M^T p; per-hit contributions
+// go to a 16-float-per-Gaussian accumulator with float4 atomics, and a finalize kernel maps
+// dL/dM to the quaternion and scales through M = S^-1 R(q)^T.
 //
 // Launch modes: plain (one launch per camera, one warp per 32-ray tile) and persistent (one
 // launch over every camera's tiles, warps pull tiles from a device counter).
@@ -846,7 +848,8 @@ __device__ __forceinline__ void trace_backward(const float4* __restrict__ rec, c
 }
 
 // ---------------------------------------------------------------------------------------------
-// Warp-aggregated gradient scatter (packet adjoints; the whole warp calls it, converged).
+// Warp-aggregated gradient scatter (the depth-first packet adjoint; the whole warp calls it,
+// converged; the best-first re-traversal and the list replay use per-lane atomics instead).
 // Each lane offers its 16-float contribution (dM rows + dm, dopacity + drgb) to the Gaussian
 // in Morton position j (j < 0: nothing).  Lanes holding a Gaussian nobody else holds issue
 // their four float4 atomics at once; lanes sharing a Gaussian are summed into the group's
