@@ -761,6 +761,7 @@ def run_ours(args):
                 "launch and one persistent re-traversal launch over the overflow tiles; CUDA graph",
         "tune": tune_b.as_dict(), "autotune": autotune, "step_ms": step_ms, "parity": parity,
         "fwd_mrays_s": P / ms_f / 1e3 * world, "ms_per_step_fwd": ms_f,
+        "render_only_mrays_s": P / kms["fwd"] / 1e3 * world,
         "fwd_bwd_mrays_s_no_graph": P / ms_fb_nograph / 1e3 * world,
         "plain": plain,
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
