@@ -571,6 +571,31 @@ def run_ours(args):
         rr.close()
         replay = {"fwd_bwd_mrays_s": P / ms_rr / 1e3 * world, "ms_per_step_fwd_bwd": ms_rr,
                   "adjoint": "re-traversal of every ray (hit_list 0)"}
+    # the paper's adjoint variants on the same step (eager launches, the batched renderer):
+    # hits ordered by the maximum-response parameter t_m, the depth gradient, and the eps2
+    # estimator for the last meaningful Gaussian
+    variants = None
+    if not args.no_plain:
+        variants = {}
+        d_depth = torch.from_numpy(scenes.upstream_grad(P, seed=3)[1]).to(dev)
+
+        def vstep(p, depth_grad=False):
+            rb.build(*params)
+            rb.render(None, p, out=outs)
+            for t in grads.values():
+                t.zero_()
+            rb.backward(d_rgb, d_alpha, grads=grads, d_depth=d_depth if depth_grad else None)
+
+        for name, p, dg in (("sort_key_tm", RenderParams(Q=wl.Q, eps1=wl.eps1, background=wl.background,
+                                                         k_max=wl.k_max, sort_key=1), False),
+                            ("depth_gradient", prm, True),
+                            ("eps2_estimator", RenderParams(Q=wl.Q, eps1=wl.eps1, background=wl.background,
+                                                            k_max=wl.k_max, eps2=0.01), False)):
+            ms_v, _ = timed(lambda: vstep(p, dg), max(3, args.steps // 3), 1)
+            variants[name] = {"fwd_bwd_mrays_s": P / ms_v / 1e3 * world, "ms_per_step_fwd_bwd": ms_v}
+        rb.check_device()
+        variants["launches"] = "eager (no graph), batched persistent path, hit lists"
+        variants["eps2"] = 0.01
     plain = {}
     if not args.no_plain:
         ms_p_fb, _ = timed(lambda: step(rp, True), max(3, args.steps // 2), 1)
@@ -766,7 +791,8 @@ def run_ours(args):
         "plain": plain,
         "batched_over_plain_fwd_bwd": (plain["ms_per_step_fwd_bwd"] / ms_fb) if plain else None,
         "kernel_ms": kms,
-        "adjoint_without_hit_lists": replay, "training_step": train, "mirror_scene": mirror,
+        "adjoint_without_hit_lists": replay, "adjoint_variants": variants, "training_step": train,
+        "mirror_scene": mirror,
         "roofline": roofline, "build": build, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
         "clocks": clocks,
     }
