@@ -122,7 +122,7 @@ def test_gradients_invariant_to_tunables():
     retrace = [dict(kbuf=8), dict(kbuf=32), dict(leaf_size=1), dict(persistent=0), dict(tile_w=16),
                dict(traversal=0), dict(traversal=0, kbuf=8, leaf_size=1), dict(traversal=1),
                dict(traversal=2, kbuf=8, leaf_size=1), dict(smem_nodes=0), dict(smem_nodes=512, traversal=2),
-               dict(traversal=3), dict(traversal=3, kbuf=8, leaf_size=1)]
+               dict(traversal=3), dict(traversal=3, kbuf=8, leaf_size=1), dict(block_warps=1), dict(block_warps=3)]
     # ... and hit lists: the default, tiny (most rays re-traverse), mixed, and the largest
     listed = [dict(), dict(hit_list=1), dict(hit_list=3), dict(hit_list=3, traversal=0),
               dict(hit_list=2, traversal=1), dict(hit_list=4, traversal=3), dict(hit_list=4096, persistent=0)]
