@@ -279,8 +279,8 @@ rs_status rs_tune(const rs_gaussians* g, float Q_box, const rs_camera* cams, int
  *     RS_FIXED_MAX_PIXELS (each camera is checked on its own first); larger requests, and
  *     non-finite camera or render parameters, return RS_ERR_INVALID_ARG before any launch.
  *   - The first call on a device resolves the array's device address (set-up, once per
- *     device, with that device current) and caches it; make that first call before any
- *     stream capture, and make no call on a device after a cudaDeviceReset of it.
+ *     device, with that device current) and caches it; make no call on a device after a
+ *     cudaDeviceReset of it.
  *   - All calls share the array and it keeps the previous call's contents (the call clears
  *     what must start at zero): calls that overlap on the GPU race with each other.
  *   - The camera table is passed to the device as a kernel argument: no host buffer is read
@@ -321,11 +321,13 @@ rs_status rs_debug_rays(const rs_camera* cams, int32_t n_cams, int64_t n_rays,
                         float* d, void* cuda_stream);
 
 /* The renderer's ray/Gaussian test for n_pairs (ray r, sorted Gaussian j) pairs of `accel`:
- * out[6 * k .. 6 * k + 5] = D^2, t1, hit (1/0), alpha, r, b (device floats), where r is the
- * sub-ulp residual that the hit's ordering key carries below t1, decoded to units of ulp(t1)
- * (the centre of its bin, in [-1/2, 1/2]; 0 for a miss), and b the number of residual bits,
- * so that t1 + r ulp(t1) is the parameter the renderer orders hits by.  ray_o/ray_d device
- * float[3 n_pairs], sorted_j device int32[n_pairs]; out device float[6 n_pairs]. */
+ * out[8 * k .. 8 * k + 7] = D^2, t1, hit (1/0), alpha, r, b, tm, rm (device floats), where r is
+ * the sub-ulp residual that the hit's ordering key carries below t1, decoded to units of
+ * ulp(t1) (the centre of its bin, in [-1/2, 1/2]; 0 for a miss), and b the number of residual
+ * bits, so that t1 + r ulp(t1) is the parameter the renderer orders hits by; tm and rm are the
+ * same pair for the t_m ordering (sort_key 1: the key's high half max(t_m, t1) and its residual
+ * in units of ulp(tm)).  ray_o/ray_d device float[3 n_pairs], sorted_j device int32[n_pairs];
+ * out device float[8 n_pairs].  A sorted_j outside [0, n) gives NaN in all eight outputs. */
 rs_status rs_debug_hits(const rs_accel* accel, int64_t n_pairs, const float* ray_o,
                         const float* ray_d, const int32_t* sorted_j, float Q, float t_near,
                         float* out, void* cuda_stream);

@@ -103,13 +103,13 @@ def raygen_f64(cams, cam_index, px, py):
 
 def ray_gaussian(o, d, mean, quat, scale, Q, t_near=0.0, with_tol=False):
     """(D2, t1, hit, tau) of one ray against one Gaussian (Prop. 1 and 2), FP64; with_tol adds
-    the oracle's models of the uncertainty of an FP32 evaluation of t1 and of D2 (the per-hit
-    halves of its TIE and BOUNDARY bands)."""
-    out = np.zeros(6, np.float64)
+    the oracle's models of the uncertainty of an FP32 evaluation of t1, of D2 and of t_m (the
+    per-hit halves of its TIE and BOUNDARY bands; t_m's for sort key 1)."""
+    out = np.zeros(7, np.float64)
     args = [_c(x, np.float64) for x in (o, d, mean, quat, scale)]
     lib().or_ray_gaussian(*[_p(a) for a in args], float(Q), float(t_near), _p(out))
     res = (float(out[0]), float(out[1]), bool(out[2] > 0.5), float(out[3]))
-    return res + (float(out[4]), float(out[5])) if with_tol else res
+    return res + (float(out[4]), float(out[5]), float(out[6])) if with_tol else res
 
 
 def quat_to_rot(q):

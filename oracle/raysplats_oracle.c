@@ -94,16 +94,18 @@ enum {
  * per Gaussian (d2tol, a first-order model of that error, see ray_gauss); TIE uses a band per
  * pair of hits: the sum of their t-uncertainties (ttol) plus OR_T_QUANTUM units of the FP32
  * spacing at t (the renderer orders by keys resolved to a fraction of that spacing).  TNEAR
- * keeps a relative band: the renderer's t >= t_near test uses the FP32-rounded t.  On 330,000
- * hits of three scenes the measured errors stay below 3.6 (t) and 4.5 (D2) times the unscaled
- * models, so the scales below leave a margin of two.  The D2 model is capped at
- * OR_BOUNDARY_REL Q: its flat-Gaussian term assumes a worst-case rounding of the whitening, while
- * the largest measured D2 error is 7e-6 Q. */
+ * keeps a relative band: the renderer's t >= t_near test uses the FP32-rounded t.  The renderer
+ * rounds each entry of the whitening once from FP64; on 330,000 hits of three scenes its
+ * measured errors then stay below 1.9 (t1), 2.5 (t_m) and 2.7 (D2) times the unscaled models, so
+ * the scales below leave a margin of two.  The D2 model is capped at OR_BOUNDARY_REL Q: its
+ * flat-Gaussian term assumes a worst-case rounding of the whitening, while the largest measured
+ * D2 error is 3.8e-6 Q. */
 #define OR_IMPACT_TOL 1e-4
-#define OR_BOUNDARY_REL 2e-5
+#define OR_BOUNDARY_REL 1e-5
 #define OR_TIE_REL 5e-7
-#define OR_T_ERR_C 8.0
-#define OR_D2_ERR_C 10.0
+#define OR_T_ERR_C 4.0
+#define OR_TM_ERR_C 5.0
+#define OR_D2_ERR_C 6.0
 #define OR_T_QUANTUM (1.0 / 256.0)
 
 /* ------------------------------------------------------------------------------------ */
@@ -249,8 +251,8 @@ static void ray_gauss(const double o[3], const double d[3], const double m[3], c
      * isotropic Gaussian, up to s_max / s_min for a flat one seen edge-on), and moves D2 by
      * about 2 D |v| / s_min (v = w + tm_r d, the closest-approach offset); an error of D2 enters
      * t1 amplified by 1 / (2 a r), i.e. by D / sqrt(Q - D2) relative to the terms above.  These
-     * are models, not bounds: OR_T_ERR_C and OR_D2_ERR_C scale them to cover the FP32 errors
-     * measured on the renderer's solve with a margin of two. */
+     * are models, not bounds: OR_T_ERR_C, OR_TM_ERR_C and OR_D2_ERR_C scale them to cover the
+     * FP32 errors measured on the renderer's solve with a margin of two. */
     g->ttol = g->mtol = g->d2tol = 0.0;
     if (g->D2 > 1.01 * Q) return; /* far from a hit: no decision to flag */
     const double od = om[0] * d[0] + om[1] * d[1] + om[2] * d[2];
@@ -274,14 +276,15 @@ static void ray_gauss(const double o[3], const double d[3], const double m[3], c
     const double r = sqrt(gap / g->a);
     const double amp = gap > 0.0 ? D / sqrt(gap) : INFINITY;
     g->ttol = OR_T_ERR_C * u * (kk * (wn + fabs(tmr) + r) * (1.0 + amp) + wn + r);
-    g->mtol = OR_T_ERR_C * u * (kk + 1.0) * (wn + fabs(tmr));
+    g->mtol = OR_TM_ERR_C * u * (kk + 1.0) * (wn + fabs(tmr));
 }
 
 /* Exported for unit pins: one ray (double) against one Gaussian given by (mean, quat, scale).
  * out[0] = D2, out[1] = t1, out[2] = hit flag (1/0), out[3] = tau = <o',d'>/<d',d'>,
- * out[4] = the t1 uncertainty model (ttol), out[5] = the D2 uncertainty model (d2tol). */
+ * out[4] = the t1 uncertainty model (ttol), out[5] = the D2 uncertainty model (d2tol),
+ * out[6] = the t_m uncertainty model (mtol). */
 void or_ray_gaussian(const double o[3], const double d[3], const double m[3], const double q[4],
-                     const double s[3], double Q, double t_near, double out[6]) {
+                     const double s[3], double Q, double t_near, double out[7]) {
     double M[9];
     or_geom g;
     whitening(q, s, M);
@@ -292,6 +295,7 @@ void or_ray_gaussian(const double o[3], const double d[3], const double m[3], co
     out[3] = g.tau;
     out[4] = g.ttol;
     out[5] = g.d2tol;
+    out[6] = g.mtol;
 }
 
 /* ------------------------------------------------------------------------------------ */

@@ -11,8 +11,8 @@
 // RS_FIXED_MAX_CAMERAS; the array is about 12 MB and every GPU that loads the library holds
 // it until the process exits.  The first call on a device resolves the array's device address
 // (cudaGetSymbolAddress with that device current) and caches it for the life of the process;
-// make that first call before any stream capture, and do not call the entry point again on a
-// device after cudaDeviceReset (the cached address belongs to the context that was reset).
+// do not call the entry point again on a device after cudaDeviceReset (the cached address
+// belongs to the context that was reset).
 // Calls share the array and keep the previous call's contents, so calls that overlap on the
 // GPU (different streams, or different host threads on the same device) race; the entry point
 // itself clears everything that must start at zero.  The camera table travels as a kernel

@@ -103,10 +103,10 @@ __global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs
                              const int32_t* sj, float Q, float t_near, float* out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_pairs) return;
-    float* o = out + 6 * k;
+    float* o = out + 8 * k;
     const int j = sj[k];
     if (j < 0 || j >= n_gauss) {  // out-of-range id: report NaN instead of reading
-        for (int c = 0; c < 6; ++c) o[c] = __int_as_float(0x7fc00000);
+        for (int c = 0; c < 8; ++c) o[c] = __int_as_float(0x7fc00000);
         return;
     }
     Hit h;
@@ -117,11 +117,17 @@ __global__ void k_debug_hits(const float4* rec, int64_t n_gauss, int64_t n_pairs
     o[1] = h.t1;
     o[2] = h.hit ? 1.f : 0.f;
     o[3] = response_alpha(rec[4 * j + 3].x, h.D2);
-    // the ordering key's sub-ulp residual, decoded to units of ulp(t1): the centre of its bin
+    // the ordering keys' sub-ulp residuals, decoded to units of ulp of their high half: the
+    // centre of the residual's bin (sort key 0: t1; sort key 1: max(t_m, t1))
     const int jb = key_id_bits((int)n_gauss), sb = 32 - jb;
-    const uint32_t sub = h.hit ? (uint32_t)((uint64_t)hit_key(h, 0, j, jb) >> jb) & ((1u << sb) - 1u) : 0u;
-    o[4] = h.hit ? (float)(((double)sub + 0.5) / (double)(1ull << sb) - 0.5) : 0.f;
+    const uint32_t smask = (1u << sb) - 1u;
+    const double bins = (double)(1ull << sb);
+    const uint32_t sub = h.hit ? (uint32_t)((uint64_t)hit_key(h, 0, j, jb) >> jb) & smask : 0u;
+    const uint32_t subm = h.hit ? (uint32_t)((uint64_t)hit_key(h, 1, j, jb) >> jb) & smask : 0u;
+    o[4] = h.hit ? (float)(((double)sub + 0.5) / bins - 0.5) : 0.f;
     o[5] = (float)sb;
+    o[6] = hit_key_t(h, 1);
+    o[7] = h.hit ? (float)(((double)subm + 0.5) / bins - 0.5) : 0.f;
 }
 
 

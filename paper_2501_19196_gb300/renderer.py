@@ -169,7 +169,7 @@ class Renderer:
 
     def debug_hits(self, ray_o, ray_d, sorted_j, Q, t_near=0.0, stream=None):
         n = sorted_j.numel()
-        out = torch.empty((n, 6), device=ray_o.device, dtype=torch.float32)
+        out = torch.empty((n, 8), device=ray_o.device, dtype=torch.float32)
         native.check(self.lib.rs_debug_hits(self._accel, n, _ptr(ray_o), _ptr(ray_d), _ptr(sorted_j), float(Q),
                                             float(t_near), _ptr(out), _stream_handle(stream)))
         return out

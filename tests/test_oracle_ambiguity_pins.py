@@ -11,7 +11,7 @@ construction, or clearly not one:
 * BOUNDARY: a sphere whose Mahalanobis distance to the ray is sqrt(Q (1 - 5e-7)) is a hit by a
   hair -> BOUNDARY and IMPACT (toggling it changes the colour by about opacity * e^{-Q/2});
   at Q (1 - 1e-4) it is a clear hit -> no flag (the per-Gaussian FP32 band of a sphere is about
-  2e-6 Q).
+  1e-6 Q).
 * EPS1: a central hit with opacity 1 - 1e-4 leaves T = eps1 when eps1 is set to 1 minus that
   (FP32) opacity -> EPS1; opacity 0.5 -> none.
 """
