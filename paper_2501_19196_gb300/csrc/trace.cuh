@@ -134,11 +134,13 @@ __device__ __forceinline__ RayCone warp_ray_cone(const float3 o, const float3 d)
     return c;
 }
 
-// leaf_sphere_mask behind a cone pre-test: lane g tests sphere start + g against the warp's ray
-// cone, and only the spheres the cone may reach get the per-lane test (same result: the cone
-// test is conservative and the per-lane test decides).  A sphere (c, r) can meet a ray of the
-// cone at t >= 0 only if the origin lies inside it, or its centre is ahead (<w, axis> > -r) and
-// its distance to the cone's surface, |w x axis| cos - <w, axis> sin, is at most r.
+// The leaf pre-test of rays that share an origin: lane g tests sphere start + g against the
+// warp's ray cone, and the spheres the cone may reach go straight to the full test of every lane
+// that wants the leaf (the full test decides, so the result is the same as with a per-lane
+// sphere test; that test, four shuffles and a sphere/ray test per candidate, cost more than
+// the full tests it saved).  A sphere (c, r) can meet a ray of the cone at t >= 0 only if the
+// origin lies inside it, or its centre is ahead (<w, axis> > -r) and its distance to the cone's
+// surface, |w x axis| cos - <w, axis> sin, is at most r.
 __device__ __forceinline__ uint32_t leaf_sphere_mask_cone(const float4* __restrict__ sph, int start, int num,
                                                           bool want, const float3 o, const float3 d,
                                                           const RayCone& cone) {
@@ -157,19 +159,8 @@ __device__ __forceinline__ uint32_t leaf_sphere_mask_cone(const float4* __restri
         const float dperp = sqrt_approx(cx * cx + cy * cy + cz * cz);
         reach = L2 <= r * r || (t > -r && dperp * cone.cth - t * cone.sth <= r);
     }
-    uint32_t cand = __ballot_sync(FULL, reach);
-    uint32_t mask = 0;
-    while (cand) {
-        const int g = __ffs(cand) - 1;
-        cand &= cand - 1;
-        float4 sp;
-        sp.x = __shfl_sync(FULL, mine.x, g);
-        sp.y = __shfl_sync(FULL, mine.y, g);
-        sp.z = __shfl_sync(FULL, mine.z, g);
-        sp.w = __shfl_sync(FULL, mine.w, g);
-        if (want && sphere_may_hit(o, d, sp)) mask |= 1u << g;
-    }
-    return mask;
+    const uint32_t cand = __ballot_sync(FULL, reach);
+    return want ? cand : 0u;
 }
 
 // The children of one node as seen by the traversal: W = 2 reads a binary node (possibly staged
