@@ -677,30 +677,70 @@ def run_ours(args):
     if not args.no_e2e:
         pinned_in = [torch.from_numpy(a).pin_memory() for a in host] + \
                     [torch.from_numpy(g_rgb_h).pin_memory(), torch.from_numpy(g_alpha_h).pin_memory()]
-        dev_in = params + [d_rgb, d_alpha]
         pinned_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
         h2d = sum(t.numel() * t.element_size() for t in pinned_in)
         d2h = sum(t.numel() * t.element_size() for t in pinned_out.values())
 
-        def e2e_step():
-            for h, d in zip(pinned_in, dev_in):
-                d.copy_(h, non_blocking=True)
-            g_fb.replay()
-            for k, v in grads.items():
-                pinned_out[k].copy_(v, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+        # A pipelined loop, as a training loop would run it: two sets of device buffers (inputs,
+        # gradients) with their own graphs (rebuild + render, adjoint); step i's inputs cross on
+        # a copy stream and its gradients return on another while the steps before and after it
+        # compute.  Every step still copies all of its inputs in and its gradients out.
 
-        for _ in range(2):
-            e2e_step()
+        def adjoint_on(dr, da, gr):
+            def fn():
+                for t in gr.values():
+                    t.zero_()
+                rb.backward(dr, da, grads=gr)
+            return fn
+
+        sets = [(params, d_rgb, d_alpha, grads, g_f, capture(adjoint_on(d_rgb, d_alpha, grads)), pinned_out)]
+        p1 = [t.clone() for t in params]
+        dr1, da1 = d_rgb.clone(), d_alpha.clone()
+        gr1 = {k: torch.zeros_like(v) for k, v in grads.items()}
+        gf1 = capture(lambda: (rb.build(*p1), rb.render(None, prm, out=outs)))
+        sets.append((p1, dr1, da1, gr1, gf1, capture(adjoint_on(dr1, da1, gr1)),
+                     {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}))
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def e2e_run(k):
+            main = torch.cuda.current_stream()
+            free = [None, None]  # set j may be overwritten once this event fires
+            for i in range(k):
+                pj, drj, daj, grj, gfj, gbj, poj = sets[i % 2]
+                with torch.cuda.stream(s_in):
+                    if free[i % 2] is not None:
+                        s_in.wait_event(free[i % 2])
+                    for h, d in zip(pinned_in, pj + [drj, daj]):
+                        d.copy_(h, non_blocking=True)
+                    ev_in = torch.cuda.Event()
+                    ev_in.record(s_in)
+                main.wait_event(ev_in)
+                gfj.replay()
+                gbj.replay()
+                ev_done = torch.cuda.Event()
+                ev_done.record(main)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done)
+                    for kk, v in grj.items():
+                        poj[kk].copy_(v, non_blocking=True)
+                    free[i % 2] = torch.cuda.Event()
+                    free[i % 2].record(s_out)
+            torch.cuda.synchronize()
+
+        e2e_run(2)
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            e2e_step()
+        e2e_run(args.steps)
         barrier()
         ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world, dev)
         e2e = {"value": job_mrays_s(P, ms_e2e, world), "unit": "Mrays/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
-               "path": "pinned host params + dL -> device, graph replay, gradients -> pinned host"}
+               "path": "every step: pinned host params + dL -> device on a copy stream, rebuild + render "
+                       "and adjoint graphs, gradients -> pinned host on a second copy stream; two buffer "
+                       "sets, so a step's copies overlap its neighbours' compute"}
+        del sets, gf1
+        # the graphs above leave the renderer's scene pointers at the second set: point them back
+        rb.build(*params)
 
     # --- full training step: activations, rebuild, render, L2 + D-SSIM loss, adjoint, Adam ---
     train = None
