@@ -37,14 +37,14 @@ L2_FLUSH_BYTES = 256 << 20
 # the 16-camera workload by its rays (x 22.615; profiles/k_render_fwd_k_replay_list_dram_traffic_
 # 1m_gaussians_2x640x416.md).  Reported only while the kernel sources are unchanged (hash).
 KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
-TRAFFIC = {"kernels": "dab06e94cee25dfc", "fwd_bytes": 6.017e9, "bwd_bytes": 6.345e9}
+TRAFFIC = {"kernels": "28835827285d2c00", "fwd_bytes": 6.015e9, "bwd_bytes": 6.444e9}
 # from the small-case --set full profiles of the same sources, per kernel (forward, list replay):
 # the fraction of cycles with an instruction issued (smsp__issue_active), the L2 hit rate
 # (lts__t_sector_hit_rate) and the active lanes per warp instruction over 32
 # (smsp__thread_inst_executed_per_inst_executed / 32, the warp execution efficiency)
-ISSUE_ACTIVE = {"kernels": "dab06e94cee25dfc", "fwd": 0.6495, "bwd": 0.3725}
-L2_HIT = {"kernels": "dab06e94cee25dfc", "fwd": 0.8430, "bwd": 0.6805}
-WARP_EFF = {"kernels": "dab06e94cee25dfc", "fwd": 23.85 / 32, "bwd": 25.68 / 32}
+ISSUE_ACTIVE = {"kernels": "28835827285d2c00", "fwd": 0.6490, "bwd": 0.6805}
+L2_HIT = {"kernels": "28835827285d2c00", "fwd": 0.8433, "bwd": 0.7610}
+WARP_EFF = {"kernels": "28835827285d2c00", "fwd": 23.85 / 32, "bwd": 27.07 / 32}
 
 
 def parse():

@@ -9,8 +9,13 @@ namespace rs {
 // List replay (adjoint, first launch): one warp per ray tile of the forward pass; every ray
 // whose hits all fit in its hit list is replayed from it (replay_list).  A tile holding a ray
 // with more hits is appended to the overflow list, which k_render_bwd re-traverses next.
+// Dynamic shared memory: the threads' gradient staging slots (list_stage_bytes).
+static size_t list_stage_bytes(int block) { return (size_t)block * BulkScatter::kFloat4 * sizeof(float4); }
+
 template <bool PERSIST, bool COUNT, bool DEPTH>
 __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
+    extern __shared__ float4 s_stage[];
+    BulkScatter sc(s_stage + BulkScatter::kFloat4 * threadIdx.x);
     const int lane = threadIdx.x & 31;
     int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     Counters cnt;
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
         }
         if (COUNT && n > 0) ++rays;
         if (COUNT) listed += nl;
-        replay_list<COUNT, DEPTH>(A.rec, A.P, pix, o, d, Tf, nl, g, B.gtmp, cnt, A.err);
+        replay_list<COUNT, DEPTH>(A.rec, A.P, pix, o, d, Tf, nl, g, B.gtmp, cnt, A.err, sc);
         if (__any_sync(0xffffffffu, n > A.P.list_cap) && lane == 0) {
             const int64_t global = A.cam_single < 0 ? tile : A.cams[A.cam_single].tile_base + tile;
             const unsigned long long slot = atomicAdd(A.queue + 3, 1ull);
@@ -59,6 +64,7 @@ __global__ void __launch_bounds__(128, 8) k_replay_list(FwdArgs A, BwdArgs B) {
         }
         if (!PERSIST) break;
     }
+    sc.drain();
     if (COUNT) {
         unsigned long long v[kNumStats] = {rays, 0, 0, cnt.hits, 0, 0, 0, listed, 0, 0};
 #pragma unroll
@@ -328,7 +334,8 @@ cudaError_t launch_backward(const FwdArgs& A, const BwdArgs& B, int K, bool pers
 template <bool PERSIST, bool COUNT, bool DEPTH>
 static int list_occupancy(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_replay_list<PERSIST, COUNT, DEPTH>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_replay_list<PERSIST, COUNT, DEPTH>, block,
+                                                  list_stage_bytes(block));
     return nb;
 }
 
@@ -342,11 +349,11 @@ template <bool DEPTH>
 static void launch_list_d(const FwdArgs& A, const BwdArgs& B, bool persistent, bool count, int grid, int block,
                           cudaStream_t st) {
     if (persistent) {
-        if (count) k_replay_list<true, true, DEPTH><<<grid, block, 0, st>>>(A, B);
-        else k_replay_list<true, false, DEPTH><<<grid, block, 0, st>>>(A, B);
+        if (count) k_replay_list<true, true, DEPTH><<<grid, block, list_stage_bytes(block), st>>>(A, B);
+        else k_replay_list<true, false, DEPTH><<<grid, block, list_stage_bytes(block), st>>>(A, B);
     } else {
-        if (count) k_replay_list<false, true, DEPTH><<<grid, block, 0, st>>>(A, B);
-        else k_replay_list<false, false, DEPTH><<<grid, block, 0, st>>>(A, B);
+        if (count) k_replay_list<false, true, DEPTH><<<grid, block, list_stage_bytes(block), st>>>(A, B);
+        else k_replay_list<false, false, DEPTH><<<grid, block, list_stage_bytes(block), st>>>(A, B);
     }
 }
 
