@@ -394,7 +394,8 @@ __global__ void __launch_bounds__(128, 4) k_render_scene(SceneArgs S) {
 
 // dL/dalpha of Gaussian j on the ray (o, d) -> the 16-float accumulator (App. A.6 chain)
 __device__ __forceinline__ void alpha_to_params(const float4* __restrict__ rec, int j, const float3 o, const float3 d,
-                                                const TraceParams& P, float tmin, float dLda, float4* __restrict__ gtmp) {
+                                                const TraceParams& P, float tmin, float dLda, float4* __restrict__ gtmp,
+                                                BulkScatter& sc) {
     const float4 g0 = __ldg(rec + 4 * j + 0), g1 = __ldg(rec + 4 * j + 1), g2 = __ldg(rec + 4 * j + 2);
     const float4 sh = __ldg(rec + 4 * j + 3);
     Hit h;
@@ -404,15 +405,18 @@ __device__ __forceinline__ void alpha_to_params(const float4* __restrict__ rec, 
     const float a = __fmul_rn(sh.x, e);
     const float gD2 = -0.5f * a * dLda;
     const float q0 = 2.f * gD2 * h.p[0], q1 = 2.f * gD2 * h.p[1], q2 = 2.f * gD2 * h.p[2];
-    float4* gp = gtmp + 4 * j;
-    atomicAdd(gp + 0, make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], -(g0.x * q0 + g1.x * q1 + g2.x * q2)));
-    atomicAdd(gp + 1, make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], -(g0.y * q0 + g1.y * q1 + g2.y * q2)));
-    atomicAdd(gp + 2, make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], -(g0.z * q0 + g1.z * q1 + g2.z * q2)));
-    atomicAdd(gp + 3, make_float4(dLda * e, 0.f, 0.f, 0.f));
+    const float4 v[4] = {make_float4(q0 * h.v[0], q0 * h.v[1], q0 * h.v[2], -(g0.x * q0 + g1.x * q1 + g2.x * q2)),
+                         make_float4(q1 * h.v[0], q1 * h.v[1], q1 * h.v[2], -(g0.y * q0 + g1.y * q1 + g2.y * q2)),
+                         make_float4(q2 * h.v[0], q2 * h.v[1], q2 * h.v[2], -(g0.z * q0 + g1.z * q1 + g2.z * q2)),
+                         make_float4(dLda * e, 0.f, 0.f, 0.f)};
+    sc.add(gtmp + 4 * j, v);
 }
 
+// Dynamic shared memory: the threads' gradient staging slots (BulkScatter, as the list replay).
 template <bool DEPTH>
 __global__ void __launch_bounds__(128) k_scene_bwd(SceneArgs S, BwdArgs B) {
+    extern __shared__ float4 s_stage[];
+    BulkScatter sc(s_stage + BulkScatter::kFloat4 * threadIdx.x);
     const FwdArgs& A = S.F;
     const int lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -441,9 +445,7 @@ __global__ void __launch_bounds__(128) k_scene_bwd(SceneArgs S, BwdArgs B) {
         float4 v[4];
         if (DEPTH && seg == 0) adjoint_hit<true>(A.rec, j, o, d, A.P, s, g, v);
         else adjoint_hit<false>(A.rec, j, o, d, A.P, s, g, v);
-        float4* gp = B.gtmp + 4 * j;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) atomicAdd(gp + q, v[q]);
+        sc.add(B.gtmp + 4 * j, v);
     }
     const int nsh = S.ssn[pix];
     if (nsh > 0) {
@@ -463,9 +465,10 @@ __global__ void __launch_bounds__(128) k_scene_bwd(SceneArgs S, BwdArgs B) {
                                  A.P.Q, S.eps_off, h);
             const float a = response_alpha(__ldg(A.rec + 4 * j + 3).x, h.D2);
             // d(T_f a T_s)/dalpha_j = -T_f a T_s / (1 - alpha_j)  (1 - alpha_j >= 1e-4)
-            alpha_to_params(A.rec, j, o, d, A.P, S.eps_off, -ga * Ts / (1.f - a), B.gtmp);
+            alpha_to_params(A.rec, j, o, d, A.P, S.eps_off, -ga * Ts / (1.f - a), B.gtmp, sc);
         }
     }
+    sc.drain();
 }
 
 }  // namespace
@@ -781,8 +784,9 @@ rs_status rs_render_scene_backward(const rs_gaussians* g, const rs_accel* accel,
         return cuda_check("scene gradient scratch reset");
     BwdArgs B{dl->d_rgb, dl->d_alpha, dl->d_depth, S->gtmp, nullptr, 0};
     const int grid = (int)((S->args.F.total_tiles + 3) / 4);
-    if (dl->d_depth) k_scene_bwd<true><<<std::max(grid, 1), 128, 0, s>>>(S->args, B);
-    else k_scene_bwd<false><<<std::max(grid, 1), 128, 0, s>>>(S->args, B);
+    const size_t stage = (size_t)128 * BulkScatter::kFloat4 * sizeof(float4);
+    if (dl->d_depth) k_scene_bwd<true><<<std::max(grid, 1), 128, stage, s>>>(S->args, B);
+    else k_scene_bwd<false><<<std::max(grid, 1), 128, stage, s>>>(S->args, B);
     const cudaError_t e = launch_finalize(S->gtmp, accel->rec, accel->vals[0], g->quats, g->scales, g->n, *out, s);
     if (e != cudaSuccess) return set_error(RS_ERR_CUDA, "scene finalize launch: %s", cudaGetErrorString(e));
     return cuda_check("scene backward launch");
