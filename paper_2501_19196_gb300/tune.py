@@ -50,13 +50,10 @@ def autotune(params5, cams, render_params, d_rgb=None, d_alpha=None, cands=None,
     P = int(sum(c.width * c.height for c in cam_arr))
     key = cache_key(n, P, len(cam_arr), d_rgb is not None)
     path = cache_path or default_cache_path()
-    if cache and os.path.exists(path):
-        try:
-            db = json.load(open(path))
-            if key in db:
-                return native.RsTuneParams(**db[key]["best"]), db[key].get("ms", {})
-        except Exception:
-            pass
+    if cache:
+        hit = cache_load(path, key)
+        if hit is not None:
+            return native.RsTuneParams(**hit["best"]), hit.get("ms", {})
     cands = cands or candidates()
     arr = (native.RsTuneParams * len(cands))(*cands)
     dev = params5[0].device
@@ -78,15 +75,41 @@ def autotune(params5, cams, render_params, d_rgb=None, d_alpha=None, cands=None,
                              None if grads is None else ctypes.byref(grads), ctypes.byref(best), ms, s))
     table = {json.dumps(c.as_dict(), sort_keys=True): float(m) for c, m in zip(cands, ms)}
     if cache:
-        db = {}
-        if os.path.exists(path):
-            try:
-                db = json.load(open(path))
-            except Exception:
-                db = {}
-        db[key] = {"best": best.as_dict(), "ms": table}
-        os.makedirs(os.path.dirname(path), exist_ok=True)
-        with open(path + ".tmp", "w") as f:
-            json.dump(db, f, indent=1)
-        os.replace(path + ".tmp", path)
+        cache_store(path, key, {"best": best.as_dict(), "ms": table})
     return best, table
+
+
+def cache_load(path, key):
+    """The cached entry for key, or None (no file, no entry, or a file being replaced)."""
+    try:
+        with open(path) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
+def cache_store(path, key, entry):
+    """Add entry under key.  Best effort: several processes (one per GPU) may store at once;
+    each writes its own temporary file and renames it over the cache, so a reader sees a whole
+    file, and the last rename wins (an entry another process stored meanwhile may be lost and
+    is then measured again)."""
+    db = {}
+    try:
+        with open(path) as f:
+            db = json.load(f)
+        if not isinstance(db, dict):
+            db = {}
+    except (OSError, ValueError):
+        db = {}
+    db[key] = entry
+    tmp = f"{path}.{os.getpid()}.tmp"
+    try:
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        try:
+            os.remove(tmp)
+        except OSError:
+            pass
