@@ -237,7 +237,10 @@ rs_status rs_render_counted(const rs_gaussians* g, const rs_accel* accel, const 
 /* Adjoint of the last rs_render recorded in `state` (App. A.3-A.6): replays every ray back
  * to front (from its hit list, or by re-traversing `accel`; see hit_list), recovers the
  * transmittance from the stored final value, and ACCUMULATES dL/d(means, quats, scales,
- * opacities, rgb) into `out`.  `g` and `accel` must be the ones the forward pass used. */
+ * opacities, rgb) into `out`.  `g` and `accel` must be the ones the forward pass used.  The
+ * sums over rays are formed by atomic FP32 additions in device memory (float4 atomics, or one
+ * 64 B bulk reduction per replayed hit), so their rounding, and the gradients' last bits,
+ * change from call to call; the forward's outputs do not. */
 rs_status rs_render_backward(const rs_gaussians* g, const rs_accel* accel,
                              const rs_fwd_state* state, const rs_frame_grad* dl,
                              const rs_tune_params* tune, rs_gaussian_grads* out,
