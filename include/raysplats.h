@@ -136,7 +136,9 @@ typedef struct {
     float* d_rgb;
 } rs_gaussian_grads;
 
-/* Tunables.  None changes a result (tests check this), only speed.
+/* Tunables.  None changes a result of rs_render (tests check this), only speed.  In scenes with
+ * triangles a shadow ray multiplies its (1 - alpha) factors in traversal order, so tunables can
+ * change the last bits of lit colours there.
  *   tile_w, tile_h  ray tile handled by one warp; tile_w * tile_h == 32
  *   kbuf            per-ray k-buffer depth: 8, 16 or 32 (with traversal 2 and 32, the
  *                   forward keeps it in shared memory instead of registers)
