@@ -66,6 +66,23 @@ def test_gradients_tiny_scenes(seed):
         assert max(errs.values()) < TOL_GRAD, (kw, errs)
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_random_scenes_cameras_and_tunables(seed):
+    """Random scene sizes, flat fractions, camera placements and frame sizes, one render setting
+    per seed, each under four adjoint configurations (hit lists, re-traversal, lists of two,
+    4-wide nodes): gradients within 1e-3 relative L2 of the oracle's."""
+    from paper_2501_19196_gb300 import native
+    rng = np.random.default_rng(1000 + seed)
+    sc = scenes.random_tiny_scene(2000 + seed, n=int(rng.integers(20, 250)), flat_frac=float(rng.uniform(0, 0.5)))
+    cams = scenes.concat_cameras(
+        [scenes.look_at_camera(tuple(rng.uniform(-3.5, 3.5, 3)), tgt, int(rng.integers(8, 40)), int(rng.integers(8, 40)),
+                               float(rng.uniform(30, 70))) for tgt in ((0, 0, 0), (0.1, 0, 0))])
+    kw = [dict(), dict(eps1=0.05), dict(k_max=3), dict(background=(0.3, 0.2, 1.0)), dict(sort_key=1)][seed % 5]
+    for tune in (dict(), dict(hit_list=0), dict(hit_list=2), dict(traversal=3)):
+        errs, bad = _grad_case(sc, cams, params(**kw), tune=native.default_tune(**tune), seed=seed)
+        assert max(errs.values()) < TOL_GRAD, (kw, tune, errs)
+
+
 def test_every_ray_scatters_into_the_same_gaussians():
     """3,072 rays all cross one large Gaussian (and most cross the three small ones in front
     of it): every lane of every warp adds into the same few 64 B accumulators at once, through
