@@ -36,15 +36,16 @@ L2_FLUSH_BYTES = 256 << 20
 # hit-list replay on two 640x416 cameras of the same scene (532,480 rays), scaled to a launch of
 # the 16-camera workload by its rays (x 22.615; profiles/k_render_fwd_k_replay_list_dram_traffic_
 # 1m_gaussians_2x640x416.md).  Reported only while the kernel sources are unchanged (hash).
-KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cu", "rs_internal.cuh")
-TRAFFIC = {"kernels": "28835827285d2c00", "fwd_bytes": 6.015e9, "bwd_bytes": 6.444e9}
+KERNEL_SOURCES = ("trace.cuh", "render_fwd.cu", "render_bwd.cuh", "render_bwd.cu", "render_bwd_depth.cu",
+                  "rs_internal.cuh")
+TRAFFIC = {"kernels": "09612d7246d67739", "fwd_bytes": 6.014e9, "bwd_bytes": 6.447e9}
 # from the small-case --set full profiles of the same sources, per kernel (forward, list replay):
 # the fraction of cycles with an instruction issued (smsp__issue_active), the L2 hit rate
 # (lts__t_sector_hit_rate) and the active lanes per warp instruction over 32
 # (smsp__thread_inst_executed_per_inst_executed / 32, the warp execution efficiency)
-ISSUE_ACTIVE = {"kernels": "28835827285d2c00", "fwd": 0.6490, "bwd": 0.6805}
-L2_HIT = {"kernels": "28835827285d2c00", "fwd": 0.8433, "bwd": 0.7610}
-WARP_EFF = {"kernels": "28835827285d2c00", "fwd": 23.85 / 32, "bwd": 27.07 / 32}
+ISSUE_ACTIVE = {"kernels": "09612d7246d67739", "fwd": 0.6482, "bwd": 0.6819}
+L2_HIT = {"kernels": "09612d7246d67739", "fwd": 0.8433, "bwd": 0.7610}
+WARP_EFF = {"kernels": "09612d7246d67739", "fwd": 23.85 / 32, "bwd": 27.07 / 32}
 
 
 def parse():

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_NAME = "libraysplats.so"
-SOURCES = ["lbvh.cu", "render_fwd.cu", "render_bwd.cu", "api.cu", "fixed_scratch.cu", "train.cu", "scene.cu"]
+SOURCES = ["lbvh.cu", "render_fwd.cu", "render_bwd.cu", "render_bwd_depth.cu", "api.cu", "fixed_scratch.cu", "train.cu", "scene.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
