@@ -1,6 +1,6 @@
 """The bench's command-line contract on CPU: its defaults (one GPU, at least three warm-up
 steps) and the reference arm (the oracle on the host cores), which must print one JSON line
-with the keys of the benchmark line (metric, value, unit, steps, warm-up, cpu_baseline, e2e)."""
+with the keys of the benchmark line (impl, value, unit, steps, cpu_baseline, e2e, config)."""
 import json
 import os
 import subprocess
